@@ -1,0 +1,70 @@
+"""FP64 value oracle: the plain product Y = A X and its iteration (test infrastructure only).
+
+Eq. 1 (Section 3) states A X = sum_i P_{pi_i} (B_i (P_{pi_i}^T X)): an
+identity, so the arrow-decomposed product reaches exactly (up to rounding
+order) the plain sparse-times-dense product.  That plain product, in FP64, is
+the value oracle.  The iteration X_{t+1} = sigma(A X_t) is the one of
+Section 2 ("Matrices"); the only sigma used here is the per-column L2
+normalisation, reduced in FP64.
+
+Pinned by tests/test_oracle_spmm.py (closed-form stencil eigenvectors,
+row-normalised and GCN-normalised invariants, dense brute force).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def spmm(A, X: np.ndarray) -> np.ndarray:
+    """Y = A X in FP64 via scipy's CSR product (Section 2: Y = A X)."""
+    S = A.to_scipy()
+    return np.asarray(S @ np.asarray(X, dtype=np.float64))
+
+
+def spmm_dense(A, X: np.ndarray) -> np.ndarray:
+    """Brute force Y = A X for tiny n: densify A entry by entry, then a dense product."""
+    n = A.n
+    D = np.zeros((n, n), dtype=np.float64)
+    for r in range(n):
+        for j in range(int(A.rowptr[r]), int(A.rowptr[r + 1])):
+            D[r, int(A.colidx[j])] += float(A.values[j])
+    return D @ np.asarray(X, dtype=np.float64)
+
+
+def column_normalise(Y: np.ndarray) -> np.ndarray:
+    """sigma of Section 2 as used here: divide every column by its FP64 L2 norm."""
+    Y = np.asarray(Y, dtype=np.float64)
+    norms = np.sqrt(np.sum(Y * Y, axis=0))
+    return Y / norms
+
+
+def iterate(A, X: np.ndarray, iters: int, rescale: bool = False) -> np.ndarray:
+    """X_T of X_{t+1} = sigma(A X_t), X_0 = X (Section 2).
+
+    sigma is the identity when ``rescale`` is false, else
+    :func:`column_normalise`.  Returns X_T in FP64.
+    """
+    S = A.to_scipy()
+    Y = np.asarray(X, dtype=np.float64)
+    for _ in range(iters):
+        Y = np.asarray(S @ Y)
+        if rescale:
+            Y = column_normalise(Y)
+    return Y
+
+
+def decomposed_product(levels, X: np.ndarray) -> np.ndarray:
+    """Eq. 1 written out: Y = sum_i P_{pi_i} (B_i (P_{pi_i}^T X)), in FP64.
+
+    Each level carries ``iperm`` (position -> vertex) and its B_i in CSR over
+    positions.  (P^T X)[p] = X[iperm[p]]; P Z puts row p of Z at vertex iperm[p].
+    """
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.zeros_like(X)
+    for lv in levels:
+        Xp = X[lv.iperm]                      # P_{pi_i}^T X
+        Zi = lv.to_scipy() @ Xp               # B_i (P_{pi_i}^T X)
+        Yi = np.zeros_like(X)
+        Yi[lv.iperm] = Zi                     # P_{pi_i} (...)
+        Y += Yi
+    return Y
