@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Benchmark of the arrow-decomposition SpMM on GB300 (prints ONE JSON line on rank 0).
+
+Default workload (one step = one arrow_spmm call = the whole hot path once):
+  3D 400x400x400 grid, 7-point stencil (n = 64,000,000, nnz = 447,040,000), values
+  U(0.5,1.5) row-normalised f32, arrow width b = 4096, X n x 16 f32 N(0,1),
+  20 iterations of X <- A X with the FP64 per-column norm rescale.
+Inputs (X 4.1 GB, A 3.6 GB) are larger than the 129 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload grid3d|grid2d|rmat] [--size S] [--iters T] [--k K] [--dtype f32|bf16]
+
+--impl reference times the CPU oracle (the FP64 product of the oracle package, as it
+stands) on a bounded sample of the same workload on the host cores.
+Under torchrun each rank runs its own replica of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "arrow-SpMM iters/s & HBM GB/s (% of peak) vs plain FP32/cuSPARSE; serve p50/p99"
+KERNEL_SRC = os.path.join(ROOT, "paper_2402_19364_gb300", "csrc", "arrow_spmm.cu")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="grid3d", choices=["grid3d", "grid2d", "rmat"])
+    p.add_argument("--size", type=int, default=0, help="grid side / R-MAT scale (0 = workload default)")
+    p.add_argument("--iters", type=int, default=0)
+    p.add_argument("--k", type=int, default=0)
+    p.add_argument("--dtype", default="", choices=["", "f32", "bf16"])
+    p.add_argument("--no-cusparse", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def workload_spec(a):
+    if a.workload == "grid3d":
+        N = a.size or 400
+        return dict(name="grid3d", N=N, b=4096, k=a.k or 16, iters=a.iters or 20, rescale=True,
+                    dtype=a.dtype or "f32", seed_a=3, seed_x=4,
+                    desc=f"3D {N}^3 grid 7-point stencil, U(0.5,1.5) row-normalised, b=4096")
+    if a.workload == "grid2d":
+        N = a.size or 64
+        return dict(name="grid2d", N=N, b=64, k=a.k or 16, iters=a.iters or 10, rescale=False,
+                    dtype=a.dtype or "f32", seed_a=1, seed_x=2,
+                    desc=f"2D {N}x{N} grid 5-point stencil, U(0.5,1.5) row-normalised, b=64")
+    s = a.size or 23
+    return dict(name="rmat", N=s, b=8192, k=a.k or 128, iters=a.iters or 8, rescale=False,
+                dtype=a.dtype or "bf16", seed_a=5, seed_x=6,
+                desc=f"R-MAT scale {s} ef16 (0.57,0.19,0.19,0.05) symmetrised + self-loops, GCN-normalised, b=8192")
+
+
+def make_matrix(spec):
+    import workloads as w
+    if spec["name"] == "grid3d":
+        return w.grid3d(spec["N"], seed=spec["seed_a"])
+    if spec["name"] == "grid2d":
+        return w.grid_stencil((spec["N"], spec["N"]), seed=spec["seed_a"])
+    return w.rmat_gcn(spec["N"], 16, seed=spec["seed_a"])
+
+
+def make_sample(spec, rows_target):
+    """A smaller matrix of the same family and structure, for the CPU oracle timing."""
+    import workloads as w
+    if spec["name"] == "grid3d":
+        N = spec["N"]
+        layers = max(1, min(N, rows_target // (N * N)))
+        return w.grid_stencil((layers, N, N), seed=spec["seed_a"]), f"{layers}x{N}x{N} slab of the same grid"
+    if spec["name"] == "grid2d":
+        return make_matrix(spec), "the whole matrix"
+    sc = max(10, min(spec["N"], int(math.log2(max(2, rows_target)))))
+    return w.rmat_gcn(sc, 16, seed=spec["seed_a"]), f"R-MAT scale {sc} of the same family"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """DRAM bytes per rows-kernel launch from the committed ncu summary, if it was taken on
+    the current kernel source (profiles/arrow_rows_traffic.txt); else None."""
+    path = os.path.join(ROOT, "profiles", "arrow_rows_traffic.txt")
+    try:
+        with open(KERNEL_SRC, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != digest:
+            return None
+        return kv
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_time(spec, rows_target, reps):
+    """Seconds per full-matrix iteration of the FP64 oracle, from a bounded sample."""
+    from oracle import spmm as S
+    import workloads as w
+    A, desc = make_sample(spec, rows_target)
+    X = w.features(A.n, spec["k"], seed=spec["seed_x"]).astype(np.float64)
+    S.iterate(A, X, 1, rescale=spec["rescale"])       # warm the caches once
+    t0 = time.perf_counter()
+    S.iterate(A, X, reps, rescale=spec["rescale"])
+    dt = time.perf_counter() - t0
+    return dt / reps, A.n, desc
+
+
+def run_reference(a, spec):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as w
+    from oracle import spmm as S
+    n_full = {"grid3d": spec["N"] ** 3, "grid2d": spec["N"] ** 2, "rmat": 1 << spec["N"]}[spec["name"]]
+    A, desc = make_sample(spec, 4_000_000)
+    X = w.features(A.n, spec["k"], seed=spec["seed_x"]).astype(np.float64)
+    for _ in range(a.warmup):
+        S.iterate(A, X, 1, rescale=spec["rescale"])
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        S.iterate(A, X, 1, rescale=spec["rescale"])
+    dt = (time.perf_counter() - t0) / a.steps
+    value = (A.n / n_full) / dt                         # full-matrix iterations per second
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec["desc"], "k": spec["k"], "iters": spec["iters"]},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one FP64 iteration of the oracle product per step on {desc} "
+                                       f"({A.n:,} of {n_full:,} rows), scaled by rows"},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    spec = workload_spec(a)
+    if a.impl == "reference":
+        run_reference(a, spec)
+        return
+    import torch
+    rank, world, local, pg = dist_init()
+    torch.cuda.set_device(local)
+    from paper_2402_19364_gb300 import build as _build
+    _build.build()
+    import paper_2402_19364_gb300 as arrow
+
+    t0 = time.perf_counter()
+    A = make_matrix(spec)
+    t_gen = time.perf_counter() - t0
+    k, iters, dt_name = spec["k"], spec["iters"], spec["dtype"]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dt_name]
+    t0 = time.perf_counter()
+    M = arrow.ArrowMatrix(A, spec["b"], value_dtype=dt_name, device=local)
+    t_dec = time.perf_counter() - t0
+    st = M.stats()
+    levels = [M.level_info(i) for i in range(M.num_levels)]
+    import workloads as w
+    Xh = torch.from_numpy(w.features(A.n, k, seed=spec["seed_x"] + 1000 * rank)).to(tdt)
+    Xd = Xh.cuda()
+    Yd = torch.empty_like(Xd)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, a.warmup)):
+        M.spmm(Xd, iters, rescale=spec["rescale"], out=Yd)
+    torch.cuda.synchronize()
+    M.profile_get(arrow.ARROW_K_ROWS)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        M.spmm(Xd, iters, rescale=spec["rescale"], out=Yd, profile=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(pg, ms_total)
+    rows_ms, rows_launches = M.profile_get(arrow.ARROW_K_ROWS)
+    seg_ms, seg_launches = M.profile_get(arrow.ARROW_K_SEGMENTS)
+    norm_ms, norm_launches = M.profile_get(arrow.ARROW_K_NORM)
+    perm_ms, perm_launches = M.profile_get(arrow.ARROW_K_PERMUTE)
+    launches = rows_launches + seg_launches + norm_launches + perm_launches
+    ms_step = ms_total / a.steps
+    value = world * a.steps * iters / (ms_total / 1e3)
+
+    ab = M.algorithmic_bytes_per_iter(k, dt_name)
+    # the rows kernel reads every entry except those of split rows (read by the segment kernel)
+    peak, peak_kind = load_peaks()
+    per_launch_s = (rows_ms + seg_ms) / max(1, rows_launches) / 1e3
+    achieved = ab["total"] / per_launch_s / 1e9
+    tr = kernel_traffic()
+    traffic = None
+    if tr is not None:
+        try:
+            traffic = float(tr["dram_bytes_per_launch_full_size"])
+        except (KeyError, ValueError):
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "arrow_rows_kernel" + (" + arrow_segments_kernel" if seg_launches else ""),
+                "algorithmic_bytes_per_launch": ab["total"], "launch_ms": per_launch_s * 1e3,
+                "frac_of_nominal_8000": achieved / 8000.0}
+
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": a.steps,
+           "warmup": max(3, a.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": dt_name, "data": "synthetic",
+           "config": {"workload": spec["desc"], "n": A.n, "nnz": A.nnz, "b": spec["b"], "k": k, "iters": iters,
+                      "rescale_fp64": spec["rescale"], "levels": [list(x) for x in levels],
+                      "long_rows": st["long_rows"], "segments": st["segments"],
+                      "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+           "roofline": roofline, "gpu_launches": launches, "clocks": clk,
+           "kernel_ms": {"rows": rows_ms / a.steps, "segments": seg_ms / a.steps, "norm": norm_ms / a.steps,
+                         "permute": perm_ms / a.steps},
+           "prep_s": {"generate": t_gen, "decompose_and_upload": t_dec, "decompose_host": st["decompose_seconds"]}}
+
+    # ---- end to end through the public call, host buffers, copies inside the timed region ----
+    if not a.no_e2e:
+        Xp = Xh.pin_memory()
+        Yp = torch.empty_like(Xp).pin_memory()
+        for _ in range(1):
+            Xd.copy_(Xp, non_blocking=True)
+            M.spmm(Xd, iters, rescale=spec["rescale"], out=Yd)
+            Yp.copy_(Yd, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier(pg)
+        e0.record(stream)
+        for _ in range(a.steps):
+            Xd.copy_(Xp, non_blocking=True)
+            M.spmm(Xd, iters, rescale=spec["rescale"], out=Yd)
+            Yp.copy_(Yd, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(pg, e0.elapsed_time(e1))
+        nb = Xp.numel() * Xp.element_size()
+        out["e2e"] = {"value": world * a.steps * iters / (ms_e2e / 1e3), "unit": "iters/s",
+                      "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "ms_per_step": ms_e2e / a.steps}
+        del Xp, Yp
+
+    # ---- cuSPARSE SpMM on the undecomposed matrix (measured comparison) ----------------------
+    if not a.no_cusparse and rank == 0:
+        try:
+            crow = torch.from_numpy(A.rowptr.astype(np.int32)).cuda()
+            col = torch.from_numpy(A.colidx).cuda()
+            vals = torch.from_numpy(A.values.astype(np.float32)).cuda().to(tdt if dt_name == "f32" else torch.float32)
+            As = torch.sparse_csr_tensor(crow, col, vals, (A.n, A.n))
+            Xc = Xd.float()
+            for _ in range(2):
+                Yc = As @ Xc
+            torch.cuda.synchronize()
+            reps = 10
+            e0.record(stream)
+            for _ in range(reps):
+                Yc = As @ Xc
+                if spec["rescale"]:
+                    Yc = Yc / torch.linalg.vector_norm(Yc.double(), dim=0).float()
+                Xc = Yc
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_it = e0.elapsed_time(e1) / reps
+            out["cusparse"] = {"iters_per_s": 1e3 / ms_it, "ms_per_iter": ms_it,
+                               "what": "torch CSR @ dense (cusparseSpMM), f32, natural vertex order"
+                                       + (", + column normalisation" if spec["rescale"] else "")}
+            del As, crow, col, vals, Xc, Yc
+            torch.cuda.empty_cache()
+        except Exception as ex:  # comparator only: report, do not fail the bench
+            out["cusparse"] = {"error": str(ex)[:200]}
+
+    # ---- CPU oracle on the host cores (bounded sample) ----------------------------------------
+    if not a.no_cpu and rank == 0:
+        s_per_iter, rows, desc = cpu_oracle_time(spec, 6_000_000, 2)
+        v = (rows / A.n) / s_per_iter
+        out["cpu_baseline"] = {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                               "sample": f"2 FP64 iterations of the oracle product on {desc} "
+                                         f"({rows:,} of {A.n:,} rows), scaled by rows"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    M.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * arrow.h -- C-ABI of the GB300 arrow-decomposition SpMM library (libarrow_gb300.so).
+ *
+ * The library computes the iterated product X_{t+1} = sigma(A X_t) of Section 2
+ * ("Matrices") through an arrow matrix decomposition A = sum_i P_{pi_i} B_i P_{pi_i}^T
+ * (Section 3, Eq. 1): each B_i has arrow-width b (non-zeros only in its first b rows,
+ * its first b columns and its b x b diagonal tiles, Section 3.1 / Fig. 2), and the
+ * P_{pi_i} are vertex permutations found by LA-Decompose (Section 4.1) with the random
+ * spanning forest arrangement (Section 4.3) and smallest-first tree layout (Section 4.4).
+ *
+ * Conventions used by every call:
+ *   - Matrices are square n x n.  Vertex v of the graph of A is row/column v.
+ *   - Dense blocks (X, Y) are row-major n x k with row stride k elements.
+ *   - Return codes: ARROW_OK (0) or a negative ARROW_E* code; after a failure
+ *     arrow_last_error() returns a message for the calling thread.
+ *   - Calls on one handle are not thread-safe; different handles are independent.
+ *   - "stream" arguments are cudaStream_t values passed as void* (NULL = legacy default stream).
+ */
+#ifndef ARROW_GB300_H
+#define ARROW_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------------- */
+#define ARROW_OK        0
+#define ARROW_EINVAL   (-1)   /* invalid argument (bad CSR, b < 2, bad k, bad dtype, ...) */
+#define ARROW_ENOMEM   (-2)   /* host or device allocation failed; no state was leaked   */
+#define ARROW_ECUDA    (-3)   /* a CUDA runtime call failed (message has the CUDA error)  */
+#define ARROW_ETIMEOUT (-4)   /* a bounded device-side wait ran out (status word set)      */
+#define ARROW_ESTATE   (-5)   /* call not valid in the handle's state (e.g. not uploaded)  */
+
+/* ---- element types ----------------------------------------------------------------- */
+typedef enum { ARROW_F32 = 0, ARROW_BF16 = 1, ARROW_F16 = 2 } arrow_dtype;
+
+/* ---- arrow predicates (shape of each B_i) ---------------------------------------- */
+/* Block-diagonal arrow (Section 3.1, Fig. 2, Alg. 1): entry at positions (r, c) belongs
+ * to B_i iff r < b or c < b or floor(r/b) == floor(c/b).  The device path requires it. */
+#define ARROW_PRED_BLOCK 0
+/* Banded arrow (Section 1 definition, 0-based): r < b or c < b or |r - c| <= b.
+ * Host-only (structure export); arrow_upload/arrow_spmm reject it with ARROW_EINVAL. */
+#define ARROW_PRED_BAND  1
+
+/* ---- input matrix ------------------------------------------------------------------ */
+/* CSR in HOST memory, caller-owned, read during arrow_decompose only (copied).
+ * rowptr[0] = 0, rowptr non-decreasing, rowptr[n] = nnz; colidx in [0, n) strictly
+ * increasing inside each row; values are float64.  nnz must be < 2^31.
+ * The matrix need not be symmetric: LA-Decompose works on the symmetric pattern of A
+ * (Section 4.1 works on graphs), and every entry keeps its own value. */
+typedef struct {
+    int64_t        n;
+    int64_t        nnz;
+    const int64_t* rowptr;
+    const int32_t* colidx;
+    const double*  values;
+} arrow_csr;
+
+/* ---- decomposition options ------------------------------------------------------- */
+#define ARROW_HOST_ONLY 0x1   /* opts.flags: build on the host, do not touch a GPU */
+
+typedef struct {
+    uint64_t seed;        /* seed of the random edge weights (Section 4.3 step 1)           */
+    int32_t  value_dtype; /* arrow_dtype the device stores A's values in (RNE from float64) */
+    int32_t  predicate;   /* ARROW_PRED_BLOCK (default) or ARROW_PRED_BAND                  */
+    int32_t  flags;       /* ARROW_HOST_ONLY or 0                                            */
+    int32_t  nthreads;    /* host threads for the decomposition; 0 = all hardware threads   */
+    int32_t  max_levels;  /* cap on the order l of the decomposition; 0 = 254               */
+    int32_t  long_row;    /* rows with more entries than this are split; 0 = default (64)   */
+    int32_t  segment;     /* entries per split segment; 0 = default (512)                   */
+    int32_t  device;      /* CUDA device ordinal for the upload; -1 = current device        */
+} arrow_opts;
+
+/* Fill *o with defaults: seed 0, F32 values, block predicate, upload, all threads. */
+int arrow_opts_default(arrow_opts* o);
+
+/* ---- handle ------------------------------------------------------------------------ */
+typedef struct arrow_handle_s* arrow_handle;   /* opaque, library-owned */
+
+/* arrow_decompose -- LA-Decompose(A, b) of Section 4.1 on the host, then (unless
+ * opts->flags has ARROW_HOST_ONLY) upload of the decomposition to the device.
+ *   A    : host CSR as above (copied; may be freed after return).
+ *   b    : arrow width, b >= 2 (Section 4.1 requires b >= 2); b >= n gives one level.
+ *   o    : options, or NULL for arrow_opts_default().
+ *   out  : receives the handle; *out is set to NULL on failure.
+ * Levels are built until no entry of A is left (the paper's stop rule "nnz(A_i) <= 2b"
+ * read as "empty").  Errors: ARROW_EINVAL (bad CSR, b < 2, too many levels),
+ * ARROW_ENOMEM, ARROW_ECUDA (upload).  On error nothing is leaked. */
+int arrow_decompose(const arrow_csr* A, int64_t b, const arrow_opts* o, arrow_handle* out);
+
+/* Upload a handle built with ARROW_HOST_ONLY to the current (or opts.device) GPU.
+ * No-op if already uploaded.  Errors: ARROW_EINVAL (band predicate), ARROW_ENOMEM, ARROW_ECUDA. */
+int arrow_upload(arrow_handle h);
+
+/* Release the handle and all host and device memory it owns.  NULL-safe.
+ * Must not be called while work that uses the handle is still running on a stream. */
+void arrow_free(arrow_handle h);
+
+/* ---- the hot path ------------------------------------------------------------------ */
+#define ARROW_RESCALE 0x1   /* spmm flags: sigma = per-column L2 normalisation (FP64 norms) */
+#define ARROW_PROFILE 0x2   /* spmm flags: record CUDA events around every kernel launch  */
+
+/* arrow_spmm -- iters steps of X_{t+1} = sigma(A X_t), X_0 = X, result X_iters in Y.
+ * A is applied as sum_i P_i B_i P_i^T X (Eq. 1, Alg. 1 / Alg. 2 computed on one GPU):
+ * X is permuted into the first level's order once, every step runs the split head-row
+ * reduction and the fused arrow-row kernel (all levels, fixed level order, no atomics),
+ * and the result is permuted back once (Section 5.1: rows stay in pi_0 order between
+ * iterations).  sigma is the identity, or with ARROW_RESCALE the division of every
+ * column by its L2 norm, reduced in FP64.
+ *   h       : uploaded handle.
+ *   X, Y    : DEVICE pointers, row-major n x k, element type x_dtype, caller-owned.
+ *             X and Y may be the same buffer.  Both must be 16-byte aligned.
+ *   k       : columns; k * sizeof(x_dtype) must be a multiple of 16 and
+ *             k / (16 / sizeof(x_dtype)) a power of two <= 32, or a multiple of 32.
+ *   iters   : >= 0; iters = 0 copies X to Y.
+ *   x_dtype : arrow_dtype of X and Y (FP32 accumulation in every case).
+ *   flags   : 0, ARROW_RESCALE and/or ARROW_PROFILE.
+ *   stream  : cudaStream_t; the call only enqueues work (no host synchronisation), except
+ *             that the first call for a given (k, x_dtype) allocates the handle's workspace.
+ * Errors: ARROW_EINVAL, ARROW_ESTATE (not uploaded), ARROW_ENOMEM, ARROW_ECUDA. */
+int arrow_spmm(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y,
+               int32_t x_dtype, int32_t flags, void* stream);
+
+/* Workspace bytes arrow_spmm_ws needs for (k, x_dtype, flags). */
+int arrow_workspace_size(arrow_handle h, int64_t k, int32_t x_dtype, int32_t flags, size_t* bytes);
+
+/* arrow_spmm with caller-provided DEVICE workspace (256-byte aligned, >= the size from
+ * arrow_workspace_size).  Makes no allocation; calls with distinct workspaces on
+ * distinct streams may overlap on one handle (the handle's device data is read-only). */
+int arrow_spmm_ws(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y,
+                  int32_t x_dtype, int32_t flags, void* workspace, size_t ws_bytes, void* stream);
+
+/* ---- structure export (parity tests, reports) ------------------------------------ */
+/* Number of levels l (order of the decomposition). */
+int arrow_num_levels(arrow_handle h, int32_t* l);
+/* Level i: active rows n_i (1 + largest position touched by an entry of B_i) and nnz(B_i). */
+int arrow_level_info(arrow_handle h, int32_t i, int64_t* n_active, int64_t* nnz);
+/* Level i: perm_out[v] = pi_i(v), the position of vertex v (host buffer of n int32). */
+int arrow_level_perm(arrow_handle h, int32_t i, int32_t* perm_out);
+/* Level i: B_i in CSR over positions 0..n-1 (host buffers: rowptr n+1, colidx and vals
+ * nnz(B_i)); columns ascending in each row; values are A's float64 values. */
+int arrow_level_csr(arrow_handle h, int32_t i, int64_t* rowptr, int32_t* colidx, double* vals);
+
+typedef struct {
+    int64_t n, nnz, b;
+    int32_t levels;
+    int32_t value_dtype;
+    int64_t long_rows;       /* rows split into segments (head rows of hubs)        */
+    int64_t segments;        /* segments of the split rows                           */
+    int64_t device_bytes;    /* bytes of device memory owned by the handle (no workspace) */
+    double  decompose_seconds;
+} arrow_stats;
+int arrow_get_stats(arrow_handle h, arrow_stats* s);
+
+/* Kernel classes reported by arrow_profile_get. */
+#define ARROW_K_ROWS     0   /* fused arrow-row kernel (band rows, folded levels, write-back) */
+#define ARROW_K_SEGMENTS 1   /* split-row segment kernel (first stage of the head-row reduction) */
+#define ARROW_K_NORM     2   /* FP64 column-norm finalize                                    */
+#define ARROW_K_PERMUTE  3   /* permute-in / permute-out gathers                             */
+
+/* arrow_profile_get -- device time of the launches recorded by arrow_spmm calls made with
+ * ARROW_PROFILE since the last arrow_profile_get, for one kernel class: total milliseconds
+ * and number of launches.  Synchronises on the recorded events, then forgets them.
+ * The events are measured on the stream the kernels were launched on. */
+int arrow_profile_get(arrow_handle h, int32_t kernel, double* total_ms, int64_t* launches);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* arrow_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARROW_GB300_H */

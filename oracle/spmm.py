@@ -68,3 +68,29 @@ def decomposed_product(levels, X: np.ndarray) -> np.ndarray:
         Yi[lv.iperm] = Zi                     # P_{pi_i} (...)
         Y += Yi
     return Y
+
+
+def iterate_rows(A, X: np.ndarray, iters: int, rows: np.ndarray) -> np.ndarray:
+    """Rows ``rows`` of A^iters X, exactly, without touching the whole matrix.
+
+    Row s of A^T X depends only on the vertices within T hops of s.  With
+    R_j the vertices within j hops of ``rows``, the restriction of A to R_T
+    iterated T times is exact on R_{T-t} after t steps, hence on ``rows`` at
+    the end.  ``X`` is any object indexable by an int64 array of vertices
+    (an ndarray, or a callable returning those rows).
+    """
+    import scipy.sparse as sp
+    S = A.to_scipy()
+    cur = np.unique(np.asarray(rows, dtype=np.int64))
+    ball = cur
+    for _ in range(iters):
+        nb = np.unique(S[cur].indices.astype(np.int64))
+        cur = np.setdiff1d(nb, ball)
+        ball = np.union1d(ball, nb)
+    sub = S[ball][:, ball]
+    Xb = X(ball) if callable(X) else np.asarray(X)[ball]
+    Y = np.asarray(Xb, dtype=np.float64)
+    for _ in range(iters):
+        Y = np.asarray(sub @ Y)
+    pos = np.searchsorted(ball, np.asarray(rows, dtype=np.int64))
+    return Y[pos]

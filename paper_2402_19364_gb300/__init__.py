@@ -1,0 +1,189 @@
+"""GB300-native arrow-decomposition SpMM (Gianinazzi et al., PPoPP 2024) -- Python binding.
+
+Thin marshalling over the C-ABI of ``include/arrow.h`` (``libarrow_gb300.so``):
+every step of the hot path runs in the library's CUDA kernels; PyTorch only
+provides device memory and streams.  If the library is missing, importing the
+handle class still works but every call raises (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import (ARROW_BF16, ARROW_F16, ARROW_F32, ARROW_HOST_ONLY, ARROW_K_NORM, ARROW_K_PERMUTE,
+                      ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_PRED_BAND, ARROW_PRED_BLOCK, ARROW_PROFILE,
+                      ARROW_RESCALE, ArrowError)
+
+__all__ = ["ArrowMatrix", "ArrowError", "dtype_code", "ARROW_F32", "ARROW_BF16", "ARROW_F16"]
+
+_DTYPE_NAMES = {"f32": ARROW_F32, "float32": ARROW_F32, "bf16": ARROW_BF16, "bfloat16": ARROW_BF16,
+                "f16": ARROW_F16, "float16": ARROW_F16}
+
+
+def dtype_code(dt) -> int:
+    """arrow_dtype code of a name ('f32', 'bf16', 'f16'), a torch dtype or a code."""
+    if isinstance(dt, int):
+        return dt
+    if isinstance(dt, str):
+        return _DTYPE_NAMES[dt]
+    import torch
+    return {torch.float32: ARROW_F32, torch.bfloat16: ARROW_BF16, torch.float16: ARROW_F16}[dt]
+
+
+def _torch_dtype(code: int):
+    import torch
+    return {ARROW_F32: torch.float32, ARROW_BF16: torch.bfloat16, ARROW_F16: torch.float16}[code]
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class ArrowMatrix:
+    """A decomposed matrix: ``arrow_decompose`` on construction, ``arrow_free`` on close.
+
+    ``A`` is any object with ``n``, ``rowptr`` (int64), ``colidx`` (int32) and
+    ``values`` (float64) in CSR form (host memory).
+    """
+
+    def __init__(self, A, b: int, *, seed: int = 0, value_dtype="f32", predicate: str = "block",
+                 host_only: bool = False, nthreads: int = 0, max_levels: int = 0, long_row: int = 0,
+                 segment: int = 0, device: int = -1):
+        L = _native.lib()
+        self._h = ctypes.c_void_p()
+        rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+        colidx = np.ascontiguousarray(A.colidx, dtype=np.int32)
+        values = np.ascontiguousarray(A.values, dtype=np.float64)
+        csr = _native.ArrowCsr(int(A.n), int(rowptr[-1]) if rowptr.size else 0, rowptr.ctypes.data,
+                               colidx.ctypes.data if colidx.size else None,
+                               values.ctypes.data if values.size else None)
+        o = _native.ArrowOpts()
+        _native.check(L.arrow_opts_default(ctypes.byref(o)))
+        o.seed = seed
+        o.value_dtype = dtype_code(value_dtype)
+        o.predicate = {"block": ARROW_PRED_BLOCK, "band": ARROW_PRED_BAND}[predicate]
+        o.flags = ARROW_HOST_ONLY if host_only else 0
+        o.nthreads = nthreads
+        o.max_levels = max_levels
+        o.long_row = long_row
+        o.segment = segment
+        o.device = device
+        _native.check(L.arrow_decompose(ctypes.byref(csr), int(b), ctypes.byref(o), ctypes.byref(self._h)))
+        self.n = int(A.n)
+        self.nnz = int(csr.nnz)
+        self.b = int(b)
+        self.value_dtype = o.value_dtype
+
+    # ---- lifetime --------------------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _native.lib().arrow_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def upload(self) -> None:
+        _native.check(_native.lib().arrow_upload(self._h))
+
+    # ---- structure export ------------------------------------------------------------
+    @property
+    def num_levels(self) -> int:
+        l = ctypes.c_int32()
+        _native.check(_native.lib().arrow_num_levels(self._h, ctypes.byref(l)))
+        return int(l.value)
+
+    def level_info(self, i: int):
+        na, nz = ctypes.c_int64(), ctypes.c_int64()
+        _native.check(_native.lib().arrow_level_info(self._h, i, ctypes.byref(na), ctypes.byref(nz)))
+        return int(na.value), int(nz.value)
+
+    def level_perm(self, i: int) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.int32)
+        _native.check(_native.lib().arrow_level_perm(self._h, i, out.ctypes.data))
+        return out
+
+    def level_csr(self, i: int):
+        _, nz = self.level_info(i)
+        rowptr = np.empty(self.n + 1, dtype=np.int64)
+        colidx = np.empty(max(nz, 1), dtype=np.int32)
+        vals = np.empty(max(nz, 1), dtype=np.float64)
+        _native.check(_native.lib().arrow_level_csr(self._h, i, rowptr.ctypes.data, colidx.ctypes.data,
+                                                    vals.ctypes.data))
+        return rowptr, colidx[:nz], vals[:nz]
+
+    def stats(self) -> dict:
+        s = _native.ArrowStats()
+        _native.check(_native.lib().arrow_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    # ---- the hot path ------------------------------------------------------------------
+    def _check_x(self, X):
+        import torch
+        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dim() == 2 and X.shape[0] == self.n
+                and X.is_contiguous()):
+            raise ValueError("X must be a contiguous CUDA tensor of shape (n, k)")
+        return dtype_code(X.dtype)
+
+    def spmm(self, X, iters: int = 1, *, rescale: bool = False, out=None, stream=None, profile: bool = False):
+        """Y = X_iters of X_{t+1} = sigma(A X_t) through ``arrow_spmm`` (returns Y)."""
+        import torch
+        xd = self._check_x(X)
+        if out is None:
+            out = torch.empty_like(X)
+        elif out.shape != X.shape or out.dtype != X.dtype or not out.is_contiguous():
+            raise ValueError("out must match X")
+        flags = (ARROW_RESCALE if rescale else 0) | (ARROW_PROFILE if profile else 0)
+        _native.check(_native.lib().arrow_spmm(self._h, ctypes.c_void_p(X.data_ptr()), X.shape[1], int(iters),
+                                               ctypes.c_void_p(out.data_ptr()), xd, flags, _stream_ptr(stream)))
+        return out
+
+    def profile_get(self, kernel: int = ARROW_K_ROWS):
+        """(total ms, launches) of the kernel class recorded by profiled calls since the last read."""
+        ms, cnt = ctypes.c_double(), ctypes.c_int64()
+        _native.check(_native.lib().arrow_profile_get(self._h, int(kernel), ctypes.byref(ms), ctypes.byref(cnt)))
+        return float(ms.value), int(cnt.value)
+
+    def workspace_size(self, k: int, dtype="f32", rescale: bool = False) -> int:
+        sz = ctypes.c_size_t()
+        _native.check(_native.lib().arrow_workspace_size(self._h, int(k), dtype_code(dtype),
+                                                         ARROW_RESCALE if rescale else 0, ctypes.byref(sz)))
+        return int(sz.value)
+
+    def spmm_ws(self, X, iters: int, workspace, *, rescale: bool = False, out=None, stream=None):
+        """``arrow_spmm_ws``: like :meth:`spmm` with a caller-owned uint8 CUDA workspace tensor."""
+        import torch
+        xd = self._check_x(X)
+        if out is None:
+            out = torch.empty_like(X)
+        flags = ARROW_RESCALE if rescale else 0
+        _native.check(_native.lib().arrow_spmm_ws(self._h, ctypes.c_void_p(X.data_ptr()), X.shape[1], int(iters),
+                                                  ctypes.c_void_p(out.data_ptr()), xd, flags,
+                                                  ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                                  _stream_ptr(stream)))
+        return out
+
+    def algorithmic_bytes_per_iter(self, k: int, x_dtype="f32") -> dict:
+        """Bytes one iteration must move (see the design notes): A's values and indices,
+        the row pointers, every level's active rows of X read once, Y written once."""
+        sv = 4 if self.value_dtype == ARROW_F32 else 2
+        sx = 4 if dtype_code(x_dtype) == ARROW_F32 else 2
+        total_active = sum(self.level_info(i)[0] for i in range(self.num_levels))
+        a_bytes = self.nnz * (sv + 4) + 4 * (self.n + 1)
+        x_bytes = total_active * k * sx
+        y_bytes = self.n * k * sx
+        return {"A": a_bytes, "X": x_bytes, "Y": y_bytes, "total": a_bytes + x_bytes + y_bytes}

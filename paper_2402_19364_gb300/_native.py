@@ -1,0 +1,95 @@
+"""ctypes declarations of the C-ABI in include/arrow.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+LIB_PATH = Path(__file__).resolve().with_name("libarrow_gb300.so")
+
+ARROW_OK = 0
+ARROW_EINVAL = -1
+ARROW_ENOMEM = -2
+ARROW_ECUDA = -3
+ARROW_ETIMEOUT = -4
+ARROW_ESTATE = -5
+ERROR_NAMES = {ARROW_EINVAL: "EINVAL", ARROW_ENOMEM: "ENOMEM", ARROW_ECUDA: "ECUDA",
+               ARROW_ETIMEOUT: "ETIMEOUT", ARROW_ESTATE: "ESTATE"}
+
+ARROW_F32, ARROW_BF16, ARROW_F16 = 0, 1, 2
+ARROW_PRED_BLOCK, ARROW_PRED_BAND = 0, 1
+ARROW_HOST_ONLY = 0x1
+ARROW_RESCALE = 0x1
+ARROW_PROFILE = 0x2
+ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_K_NORM, ARROW_K_PERMUTE = 0, 1, 2, 3
+
+
+class ArrowError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"arrow {ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ArrowCsr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("values", ctypes.c_void_p)]
+
+
+class ArrowOpts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("value_dtype", ctypes.c_int32), ("predicate", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("nthreads", ctypes.c_int32), ("max_levels", ctypes.c_int32),
+                ("long_row", ctypes.c_int32), ("segment", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class ArrowStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("b", ctypes.c_int64),
+                ("levels", ctypes.c_int32), ("value_dtype", ctypes.c_int32),
+                ("long_rows", ctypes.c_int64), ("segments", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("decompose_seconds", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_SIZE = ctypes.c_size_t
+
+# name -> (restype, argtypes); every function declared in include/arrow.h
+SIGNATURES = {
+    "arrow_opts_default": (_I32, [ctypes.POINTER(ArrowOpts)]),
+    "arrow_decompose": (_I32, [ctypes.POINTER(ArrowCsr), _I64, ctypes.POINTER(ArrowOpts), ctypes.POINTER(_P)]),
+    "arrow_upload": (_I32, [_P]),
+    "arrow_free": (None, [_P]),
+    "arrow_spmm": (_I32, [_P, _P, _I64, _I32, _P, _I32, _I32, _P]),
+    "arrow_workspace_size": (_I32, [_P, _I64, _I32, _I32, ctypes.POINTER(_SIZE)]),
+    "arrow_spmm_ws": (_I32, [_P, _P, _I64, _I32, _P, _I32, _I32, _P, _SIZE, _P]),
+    "arrow_num_levels": (_I32, [_P, ctypes.POINTER(_I32)]),
+    "arrow_level_info": (_I32, [_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "arrow_level_perm": (_I32, [_P, _I32, _P]),
+    "arrow_level_csr": (_I32, [_P, _I32, _P, _P, _P]),
+    "arrow_get_stats": (_I32, [_P, ctypes.POINTER(ArrowStats)]),
+    "arrow_profile_get": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
+    "arrow_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise ImportError(f"{LIB_PATH.name} is not built: run `python -m paper_2402_19364_gb300.build` "
+                              "(the arrow SpMM has no CPU or library fallback)")
+        L = ctypes.CDLL(str(LIB_PATH))
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != ARROW_OK:
+        msg = lib().arrow_last_error()
+        raise ArrowError(rc, msg.decode() if msg else "")

@@ -1,0 +1,76 @@
+// Internal state of an arrow handle, shared by the host decomposer (decompose.cpp)
+// and the device path (arrow_spmm.cu).  Not part of the C-ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/arrow.h"
+
+namespace arrow {
+
+void set_error(const std::string& msg);
+
+// One level i of the decomposition A = sum_i P_{pi_i} B_i P_{pi_i}^T.
+struct Level {
+    std::vector<int32_t> perm;   // vertex -> position (pi_i)
+    int64_t n_active = 0;        // 1 + largest position touched by an entry of B_i
+    int64_t nnz = 0;             // nnz(B_i)
+};
+
+// Device copy of the fused row program (see arrow_spmm.cu for how it is used).
+struct DeviceData {
+    int device = -1;
+    int32_t* rowptr = nullptr;      // [n+1] into col/val, rows in pi_0 order
+    int32_t* col = nullptr;         // [nnz] pi_0 position of the X row each entry reads
+    void* val = nullptr;            // [nnz] values, value_dtype
+    int32_t* perm0 = nullptr;       // [n]  vertex -> pi_0 position
+    int32_t* iperm0 = nullptr;      // [n]  pi_0 position -> vertex
+    int32_t* long_rows = nullptr;   // [n_long] rows (pi_0 positions) split into segments, ascending
+    int32_t* long_segptr = nullptr; // [n_long+1] first segment of each long row
+    int32_t* seg_begin = nullptr;   // [n_seg] entry range of each segment
+    int32_t* seg_end = nullptr;     // [n_seg]
+    size_t bytes = 0;
+    // handle-owned workspace (arrow_spmm); arrow_spmm_ws uses the caller's instead
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int sm_count = 0;
+};
+
+// Events recorded around kernel launches when arrow_spmm runs with ARROW_PROFILE.
+struct ProfileRecord {
+    int kind;
+    void* start;   // cudaEvent_t
+    void* stop;
+};
+
+}  // namespace arrow
+
+struct arrow_handle_s {
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int64_t b = 0;
+    arrow_opts opts{};
+    // copy of the input (values and pattern), kept for the structure export
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> colidx;
+    std::vector<double> values;
+    std::vector<uint8_t> entry_level;   // level of every entry of A
+    std::vector<arrow::Level> levels;
+    // fused row program on the host (rows in pi_0 order), uploaded by arrow_upload
+    std::vector<int32_t> f_rowptr;      // [n+1]
+    std::vector<int32_t> f_col;         // [nnz] pi_0 position of the column vertex
+    std::vector<int32_t> f_src;         // [nnz] index of the entry in A (for its value)
+    std::vector<int32_t> long_rows, long_segptr, seg_begin, seg_end;
+    double decompose_seconds = 0.0;
+    bool uploaded = false;
+    arrow::DeviceData dev;
+    std::vector<arrow::ProfileRecord> prof;       // recorded, not yet read
+    std::vector<void*> event_pool;                // free cudaEvent_t
+};
+
+namespace arrow {
+// Host decomposition (decompose.cpp).  Fills levels, entry_level and the fused row program.
+int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow_opts& o);
+}  // namespace arrow

@@ -1,0 +1,867 @@
+// Device path of the arrow-decomposition SpMM for GB300 (sm_103a), and the C-ABI.
+//
+// What runs on the GPU (one call of arrow_spmm, Eq. 1 iterated):
+//   permute-in   X^[p] = X[pi_0^{-1}(p)]                      (Section 5.1: rows are kept in
+//                                                               pi_0 order between iterations)
+//   per step t:
+//     segments   split rows (the head rows of B_0 and any other row longer than the split
+//                threshold, Alg. 1 line 2 / Lemma 5.1's row-tile tasks) are cut into
+//                fixed-size segments; one warp per segment writes an FP32 partial.
+//     rows       one team of lanes per pi_0 row p computes
+//                  Y^[p] = d_{t-1} * ( sum_{levels i in order} sum_{c in B_i row} B_i[.,c] X^[pi_0(c)] )
+//                the band rows' head-column and diagonal-tile entries (Alg. 1 line 5), and the
+//                entries of the other levels folded in through the precomputed inverse
+//                permutation (Alg. 2's reverse aggregation with destinations fixed at
+//                preprocessing, Thm. 5.2) -- a fixed order, no atomics.  Split rows add
+//                their segment partials in segment order (the second stage of the
+//                head-row reduction, Alg. 1 line 3).  With rescaling it also emits FP64
+//                per-column sums of squares of the rows it wrote.
+//     finalize   d_t[j] = 1 / sqrt(sum of the FP64 partials of column j), fixed order.
+//   permute-out  Y[v] = X^[pi_0(v)] (* d_T with rescaling)
+//
+// Every accumulation has a fixed order, so repeated calls are bit-identical.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "arrow_internal.h"
+
+namespace arrow {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+// ------------------------------------------------------------------------------------
+// element packing: one 16-byte vector of X holds V elements
+// ------------------------------------------------------------------------------------
+template <typename TX>
+struct Pack;
+
+template <>
+struct Pack<float> {
+    static constexpr int V = 4;
+    __device__ __forceinline__ static void to_float(const uint4& u, float* f) {
+        f[0] = __uint_as_float(u.x); f[1] = __uint_as_float(u.y);
+        f[2] = __uint_as_float(u.z); f[3] = __uint_as_float(u.w);
+    }
+    __device__ __forceinline__ static uint4 from_float(const float* f) {
+        return make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]), __float_as_uint(f[3]));
+    }
+};
+
+__device__ __forceinline__ void bf16x2_to_float(uint32_t w, float& lo, float& hi) {
+    lo = __uint_as_float(w << 16);
+    hi = __uint_as_float(w & 0xffff0000u);
+}
+
+template <>
+struct Pack<__nv_bfloat16> {
+    static constexpr int V = 8;
+    __device__ __forceinline__ static void to_float(const uint4& u, float* f) {
+        bf16x2_to_float(u.x, f[0], f[1]); bf16x2_to_float(u.y, f[2], f[3]);
+        bf16x2_to_float(u.z, f[4], f[5]); bf16x2_to_float(u.w, f[6], f[7]);
+    }
+    __device__ __forceinline__ static uint32_t pack2(float a, float b) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+    __device__ __forceinline__ static uint4 from_float(const float* f) {
+        return make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+    }
+};
+
+template <>
+struct Pack<__half> {
+    static constexpr int V = 8;
+    __device__ __forceinline__ static void h2(uint32_t w, float& lo, float& hi) {
+        __half2 h = *reinterpret_cast<__half2*>(&w);
+        float2 f = __half22float2(h);
+        lo = f.x; hi = f.y;
+    }
+    __device__ __forceinline__ static void to_float(const uint4& u, float* f) {
+        h2(u.x, f[0], f[1]); h2(u.y, f[2], f[3]); h2(u.z, f[4], f[5]); h2(u.w, f[6], f[7]);
+    }
+    __device__ __forceinline__ static uint32_t pack2(float a, float b) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+    __device__ __forceinline__ static uint4 from_float(const float* f) {
+        return make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+    }
+};
+
+__device__ __forceinline__ float val_to_float(float v) { return v; }
+__device__ __forceinline__ float val_to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float val_to_float(__half v) { return __half2float(v); }
+
+__device__ __forceinline__ uint4 ld_x(const void* p) {
+    uint4 r;
+    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
+    int32_t r;
+    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+template <typename TV>
+__device__ __forceinline__ TV ld_stream_val(const TV* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float ld_stream_val<float>(const float* p) {
+    float r;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(r) : "l"(p));
+    return r;
+}
+
+// ------------------------------------------------------------------------------------
+// kernels
+// ------------------------------------------------------------------------------------
+struct RowArgs {
+    const int32_t* rowptr;
+    const int32_t* col;
+    const void* val;
+    int64_t n;
+    const void* X;        // pi_0-ordered input, n x ldx
+    void* Y;              // pi_0-ordered output, n x ldx
+    int64_t ldx;          // k
+    int32_t koff;         // first column of this chunk
+    int32_t kc;           // columns of this chunk
+    int32_t long_row;     // rows with more entries are split
+    int32_t n_long;
+    const int32_t* long_rows;
+    const int32_t* long_segptr;
+    const float* partials;     // [n_seg][kc] segment partials of this chunk
+    const double* scale;       // [k] per-column factor d_{t-1}, or null
+    double* norm_partials;     // [gridDim.x][k], or null
+};
+
+template <typename TX, typename TV, int T, bool RESCALE>
+__global__ void __launch_bounds__(256) arrow_rows_kernel(RowArgs a) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    const int lane = threadIdx.x & 31;
+    const int tl = lane & (T - 1);
+    const int64_t team0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / T;
+    const int64_t nteams = (int64_t(gridDim.x) * blockDim.x) / T;
+    const int col0 = tl * V;
+    const TX* __restrict__ X = static_cast<const TX*>(a.X) + a.koff + col0;
+    TX* __restrict__ Y = static_cast<TX*>(a.Y) + a.koff + col0;
+    const TV* __restrict__ val = static_cast<const TV*>(a.val);
+
+    float scl[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) scl[v] = a.scale ? float(a.scale[a.koff + col0 + v]) : 1.0f;
+    float sq[V];
+    double dsq[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) { sq[v] = 0.f; dsq[v] = 0.0; }
+    int nsq = 0;
+
+    for (int64_t r = team0; r < a.n; r += nteams) {
+        const int32_t s = __ldg(a.rowptr + r), e = __ldg(a.rowptr + r + 1);
+        float acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.f;
+        if (e - s > a.long_row) {
+            int lo = 0, hi = a.n_long - 1;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (__ldg(a.long_rows + mid) < r) lo = mid + 1; else hi = mid;
+            }
+            const int g0 = __ldg(a.long_segptr + lo), g1 = __ldg(a.long_segptr + lo + 1);
+            for (int g = g0; g < g1; ++g) {
+                const float4* p = reinterpret_cast<const float4*>(a.partials + int64_t(g) * a.kc + col0);
+#pragma unroll
+                for (int q = 0; q < V / 4; ++q) {
+                    float4 f = p[q];
+                    acc[4 * q + 0] += f.x; acc[4 * q + 1] += f.y; acc[4 * q + 2] += f.z; acc[4 * q + 3] += f.w;
+                }
+            }
+        } else {
+            int32_t j = s;
+            for (; j + 4 <= e; j += 4) {
+                int32_t c[4];
+                float w[4];
+                uint4 x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) c[u] = ld_stream_i32(a.col + j + u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) w[u] = val_to_float(ld_stream_val<TV>(val + j + u));
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = ld_x(X + int64_t(c[u]) * a.ldx);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float f[V];
+                    P::to_float(x[u], f);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] = fmaf(w[u], f[v], acc[v]);
+                }
+            }
+            for (; j < e; ++j) {
+                const int32_t c = ld_stream_i32(a.col + j);
+                const float w = val_to_float(ld_stream_val<TV>(val + j));
+                float f[V];
+                P::to_float(ld_x(X + int64_t(c) * a.ldx), f);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = fmaf(w, f[v], acc[v]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+        const uint4 out = P::from_float(acc);
+        *reinterpret_cast<uint4*>(Y + r * a.ldx) = out;
+        if (RESCALE) {
+            float yr[V];
+            P::to_float(out, yr);
+#pragma unroll
+            for (int v = 0; v < V; ++v) sq[v] = fmaf(yr[v], yr[v], sq[v]);
+            if (++nsq == 8) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) { dsq[v] += double(sq[v]); sq[v] = 0.f; }
+                nsq = 0;
+            }
+        }
+    }
+    if (RESCALE) {
+        // FP64 column sums of squares: lanes -> warp (fixed butterfly) -> block (fixed order)
+#pragma unroll
+        for (int v = 0; v < V; ++v) dsq[v] += double(sq[v]);
+#pragma unroll
+        for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+            for (int v = 0; v < V; ++v) dsq[v] += __shfl_xor_sync(0xffffffffu, dsq[v], off);
+        __shared__ double sh[8][256];
+        const int warp = threadIdx.x >> 5;
+        if (lane < T)
+#pragma unroll
+            for (int v = 0; v < V; ++v) sh[warp][col0 + v] = dsq[v];
+        __syncthreads();
+        const int nw = blockDim.x >> 5;
+        for (int c = threadIdx.x; c < a.kc; c += blockDim.x) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sh[w][c];
+            a.norm_partials[int64_t(blockIdx.x) * a.ldx + a.koff + c] = t;
+        }
+    }
+}
+
+struct SegArgs {
+    const int32_t* seg_begin;
+    const int32_t* seg_end;
+    int64_t n_seg;
+    const int32_t* col;
+    const void* val;
+    const void* X;
+    int64_t ldx;
+    int32_t koff, kc;
+    float* partials;   // [n_seg][kc]
+};
+
+// One warp per segment of a split row; the warp's teams stride over the entries and are
+// combined with a fixed xor butterfly (first stage of the deterministic head-row reduction).
+template <typename TX, typename TV, int T>
+__global__ void __launch_bounds__(256) arrow_segments_kernel(SegArgs a) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    constexpr int TPW = 32 / T;
+    const int lane = threadIdx.x & 31;
+    const int tl = lane & (T - 1);
+    const int tw = lane / T;
+    const int col0 = tl * V;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const TX* __restrict__ X = static_cast<const TX*>(a.X) + a.koff + col0;
+    const TV* __restrict__ val = static_cast<const TV*>(a.val);
+    for (int64_t g = warp0; g < a.n_seg; g += nwarps) {
+        const int32_t s = __ldg(a.seg_begin + g), e = __ldg(a.seg_end + g);
+        float acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.f;
+        int32_t j = s + tw;
+        for (; j + 3 * TPW < e; j += 4 * TPW) {
+            int32_t c[4];
+            float w[4];
+            uint4 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c[u] = ld_stream_i32(a.col + j + u * TPW);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) w[u] = val_to_float(ld_stream_val<TV>(val + j + u * TPW));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = ld_x(X + int64_t(c[u]) * a.ldx);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float f[V];
+                P::to_float(x[u], f);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = fmaf(w[u], f[v], acc[v]);
+            }
+        }
+        for (; j < e; j += TPW) {
+            const int32_t c = ld_stream_i32(a.col + j);
+            const float w = val_to_float(ld_stream_val<TV>(val + j));
+            float f[V];
+            P::to_float(ld_x(X + int64_t(c) * a.ldx), f);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = fmaf(w, f[v], acc[v]);
+        }
+#pragma unroll
+        for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+        if (tw == 0) {
+            float4* p = reinterpret_cast<float4*>(a.partials + g * a.kc + col0);
+#pragma unroll
+            for (int q = 0; q < V / 4; ++q) p[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+    }
+}
+
+// d[j] = 1 / sqrt(sum_p partials[p][j]) in FP64; one block per column, fixed-order tree.
+__global__ void __launch_bounds__(256) arrow_norm_finalize_kernel(const double* partials, int nparts, int64_t k,
+                                                                  double* scale_out) {
+    const int64_t c = blockIdx.x;
+    double t = 0.0;
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x) t += partials[int64_t(p) * k + c];
+    __shared__ double sh[256];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scale_out[c] = sh[0] > 0.0 ? 1.0 / sqrt(sh[0]) : 1.0;
+}
+
+// dst[r] = src[idx[r]] (* scale per column), 16-byte vectors.
+template <typename TX>
+__global__ void __launch_bounds__(256) arrow_gather_rows_kernel(const TX* __restrict__ src, TX* __restrict__ dst,
+                                                                const int32_t* __restrict__ idx, int64_t n, int64_t k,
+                                                                const double* __restrict__ scale) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    const int64_t nv = k / V;
+    const int64_t total = n * nv;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = i / nv, q = i - r * nv;
+        const int64_t s = __ldg(idx + r);
+        uint4 u = ld_x(src + s * k + q * V);
+        if (scale) {
+            float f[V];
+            P::to_float(u, f);
+#pragma unroll
+            for (int v = 0; v < V; ++v) f[v] = float(double(f[v]) * scale[q * V + v]);
+            u = P::from_float(f);
+        }
+        *reinterpret_cast<uint4*>(dst + r * k + q * V) = u;
+    }
+}
+
+template <typename TV>
+__global__ void arrow_convert_values_kernel(const double* __restrict__ src, TV* __restrict__ dst, int64_t n);
+template <>
+__global__ void arrow_convert_values_kernel<float>(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        dst[i] = __double2float_rn(src[i]);
+}
+template <>
+__global__ void arrow_convert_values_kernel<__nv_bfloat16>(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                                                           int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        dst[i] = __double2bfloat16(src[i]);
+}
+template <>
+__global__ void arrow_convert_values_kernel<__half>(const double* __restrict__ src, __half* __restrict__ dst, int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        dst[i] = __double2half(src[i]);
+}
+
+// ------------------------------------------------------------------------------------
+// host helpers
+// ------------------------------------------------------------------------------------
+static size_t dtype_size(int dt) { return dt == ARROW_F32 ? 4 : 2; }
+static bool dtype_ok(int dt) { return dt >= ARROW_F32 && dt <= ARROW_F16; }
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static int cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? ARROW_ENOMEM : ARROW_ECUDA;
+}
+#define ACK(call)                                      \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+static void free_device(DeviceData& d) {
+    void* ptrs[] = {d.rowptr, d.col, d.val, d.perm0, d.iperm0, d.long_rows, d.long_segptr, d.seg_begin, d.seg_end, d.ws};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    int dev = d.device;
+    d = DeviceData{};
+    d.device = dev;
+}
+
+// ---- optional launch profiling (ARROW_PROFILE) ---------------------------------------
+struct Prof {
+    arrow_handle_s* h = nullptr;   // null: profiling off
+    cudaStream_t s = nullptr;
+    cudaEvent_t get() {
+        if (!h->event_pool.empty()) {
+            void* e = h->event_pool.back();
+            h->event_pool.pop_back();
+            return static_cast<cudaEvent_t>(e);
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t begin() {
+        if (!h) return nullptr;
+        cudaEvent_t e = get();
+        cudaEventRecord(e, s);
+        return e;
+    }
+    void end(int kind, cudaEvent_t start) {
+        if (!h) return;
+        cudaEvent_t e = get();
+        cudaEventRecord(e, s);
+        h->prof.push_back({kind, start, e});
+    }
+};
+
+static void destroy_events(arrow_handle_s* h) {
+    for (auto& r : h->prof) {
+        cudaEventDestroy(static_cast<cudaEvent_t>(r.start));
+        cudaEventDestroy(static_cast<cudaEvent_t>(r.stop));
+    }
+    for (void* e : h->event_pool) cudaEventDestroy(static_cast<cudaEvent_t>(e));
+    h->prof.clear();
+    h->event_pool.clear();
+}
+
+template <typename T>
+static int upload_vec(T** dst, const std::vector<T>& src, size_t& bytes) {
+    *dst = nullptr;
+    if (src.empty()) return ARROW_OK;
+    ACK(cudaMalloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T)));
+    bytes += src.size() * sizeof(T);
+    ACK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return ARROW_OK;
+}
+
+static int upload_impl(arrow_handle_s* h) {
+    DeviceData& d = h->dev;
+    if (h->opts.device >= 0) ACK(cudaSetDevice(h->opts.device));
+    ACK(cudaGetDevice(&d.device));
+    ACK(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, d.device));
+    int rc;
+    if ((rc = upload_vec(&d.rowptr, h->f_rowptr, d.bytes))) return rc;
+    if ((rc = upload_vec(&d.col, h->f_col, d.bytes))) return rc;
+    if ((rc = upload_vec(&d.long_rows, h->long_rows, d.bytes))) return rc;
+    if ((rc = upload_vec(&d.long_segptr, h->long_segptr, d.bytes))) return rc;
+    if ((rc = upload_vec(&d.seg_begin, h->seg_begin, d.bytes))) return rc;
+    if ((rc = upload_vec(&d.seg_end, h->seg_end, d.bytes))) return rc;
+    const int64_t n = h->n;
+    {
+        std::vector<int32_t> perm0(n), iperm0(n);
+        if (!h->levels.empty()) {
+            perm0 = h->levels[0].perm;
+            for (int64_t v = 0; v < n; ++v) iperm0[perm0[v]] = int32_t(v);
+        } else {
+            for (int64_t v = 0; v < n; ++v) perm0[v] = iperm0[v] = int32_t(v);
+        }
+        if ((rc = upload_vec(&d.perm0, perm0, d.bytes))) return rc;
+        if ((rc = upload_vec(&d.iperm0, iperm0, d.bytes))) return rc;
+    }
+    const int64_t nnz = h->nnz;
+    if (nnz > 0) {
+        std::vector<double> vals(nnz);
+        for (int64_t j = 0; j < nnz; ++j) vals[j] = h->values[h->f_src[j]];
+        double* tmp = nullptr;
+        ACK(cudaMalloc(&tmp, nnz * sizeof(double)));
+        cudaError_t e = cudaMemcpy(tmp, vals.data(), nnz * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&d.val, nnz * dtype_size(h->opts.value_dtype));
+        if (e == cudaSuccess) {
+            d.bytes += nnz * dtype_size(h->opts.value_dtype);
+            const int grid = std::max(1, std::min<int>(int((nnz + 255) / 256), d.sm_count * 16));
+            switch (h->opts.value_dtype) {
+                case ARROW_F32: arrow_convert_values_kernel<float><<<grid, 256>>>(tmp, static_cast<float*>(d.val), nnz); break;
+                case ARROW_BF16: arrow_convert_values_kernel<__nv_bfloat16><<<grid, 256>>>(tmp, static_cast<__nv_bfloat16*>(d.val), nnz); break;
+                default: arrow_convert_values_kernel<__half><<<grid, 256>>>(tmp, static_cast<__half*>(d.val), nnz); break;
+            }
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
+        cudaFree(tmp);
+        if (e != cudaSuccess) return cuda_fail(e, "arrow_upload: values");
+    }
+    return ARROW_OK;
+}
+
+// ---- launch plumbing -----------------------------------------------------------------
+struct Plan {
+    int V, T, chunks, kc;
+    int rows_grid;   // CTAs of the row kernel (= number of FP64 norm partials)
+    size_t x_bytes, part_bytes, np_bytes, sc_bytes, total;
+};
+
+static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags, Plan& p) {
+    p.V = int(16 / dtype_size(x_dtype));
+    if (k % p.V) { set_error("arrow_spmm: k * sizeof(dtype) must be a multiple of 16 bytes"); return ARROW_EINVAL; }
+    int64_t t = k / p.V;
+    if (t <= 32) {
+        if (t & (t - 1)) { set_error("arrow_spmm: k / (16 / sizeof(dtype)) must be a power of two <= 32 or a multiple of 32"); return ARROW_EINVAL; }
+        p.T = int(t); p.chunks = 1;
+    } else {
+        if (t % 32) { set_error("arrow_spmm: k / (16 / sizeof(dtype)) must be a power of two <= 32 or a multiple of 32"); return ARROW_EINVAL; }
+        p.T = 32; p.chunks = int(t / 32);
+    }
+    p.kc = p.T * p.V;
+    const int64_t teams_per_block = 256 / p.T;
+    const int64_t need = (h->n + teams_per_block - 1) / teams_per_block;
+    const int sm = h->dev.sm_count > 0 ? h->dev.sm_count : 1;
+    p.rows_grid = int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(sm) * 8)));
+    const size_t sx = dtype_size(x_dtype);
+    p.x_bytes = align256(size_t(h->n) * size_t(k) * sx);
+    p.part_bytes = align256(std::max<size_t>(1, h->seg_begin.size()) * size_t(p.kc) * 4);
+    p.np_bytes = (flags & ARROW_RESCALE) ? align256(size_t(p.rows_grid) * size_t(k) * 8) : 0;
+    p.sc_bytes = (flags & ARROW_RESCALE) ? align256(2 * size_t(k) * 8) : 0;
+    p.total = 2 * p.x_bytes + p.part_bytes + p.np_bytes + p.sc_bytes;
+    return ARROW_OK;
+}
+
+template <typename TX, typename TV, int T>
+static void launch_step(const arrow_handle_s* h, const Plan& p, const TX* cur, TX* nxt, int64_t k, float* part,
+                        const double* scale_in, double* np, cudaStream_t s, Prof& pf) {
+    const DeviceData& d = h->dev;
+    for (int ch = 0; ch < p.chunks; ++ch) {
+        const int koff = ch * p.kc;
+        if (!h->seg_begin.empty()) {
+            SegArgs sa{d.seg_begin, d.seg_end, int64_t(h->seg_begin.size()), d.col, d.val, cur, k, koff, p.kc, part};
+            const int64_t warps = int64_t(h->seg_begin.size());
+            const int grid = int(std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, int64_t(d.sm_count) * 8)));
+            cudaEvent_t e0 = pf.begin();
+            arrow_segments_kernel<TX, TV, T><<<grid, 256, 0, s>>>(sa);
+            pf.end(ARROW_K_SEGMENTS, e0);
+        }
+        const int32_t long_row = h->opts.long_row > 0 ? h->opts.long_row : 64;
+        RowArgs ra{d.rowptr, d.col, d.val, h->n, cur, nxt, k, koff, p.kc, long_row, int32_t(h->long_rows.size()),
+                   d.long_rows, d.long_segptr, part, scale_in, np};
+        cudaEvent_t e0 = pf.begin();
+        if (np)
+            arrow_rows_kernel<TX, TV, T, true><<<p.rows_grid, 256, 0, s>>>(ra);
+        else
+            arrow_rows_kernel<TX, TV, T, false><<<p.rows_grid, 256, 0, s>>>(ra);
+        pf.end(ARROW_K_ROWS, e0);
+    }
+}
+
+template <typename TX, typename TV>
+static void run_steps(const arrow_handle_s* h, const Plan& p, TX* xa, TX* xb, int64_t k, int iters, int flags, float* part,
+                      double* np, double* sc, cudaStream_t s, TX** final_buf, Prof& pf) {
+    TX* cur = xa;
+    TX* nxt = xb;
+    const bool rescale = flags & ARROW_RESCALE;
+    for (int t = 1; t <= iters; ++t) {
+        const double* sin = (rescale && t > 1) ? sc + ((t - 1) & 1) * k : nullptr;
+        double* npo = rescale ? np : nullptr;
+        switch (p.T) {
+            case 1: launch_step<TX, TV, 1>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
+            case 2: launch_step<TX, TV, 2>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
+            case 4: launch_step<TX, TV, 4>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
+            case 8: launch_step<TX, TV, 8>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
+            case 16: launch_step<TX, TV, 16>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
+            default: launch_step<TX, TV, 32>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
+        }
+        if (rescale) {
+            cudaEvent_t e0 = pf.begin();
+            arrow_norm_finalize_kernel<<<int(k), 256, 0, s>>>(np, p.rows_grid, k, sc + (t & 1) * k);
+            pf.end(ARROW_K_NORM, e0);
+        }
+        std::swap(cur, nxt);
+    }
+    *final_buf = cur;
+}
+
+template <typename TX>
+static int spmm_typed(const arrow_handle_s* h, const Plan& p, const void* X, int64_t k, int iters, void* Y, int flags,
+                      char* ws, cudaStream_t s, Prof& pf) {
+    const DeviceData& d = h->dev;
+    TX* xa = reinterpret_cast<TX*>(ws);
+    TX* xb = reinterpret_cast<TX*>(ws + p.x_bytes);
+    float* part = reinterpret_cast<float*>(ws + 2 * p.x_bytes);
+    double* np = reinterpret_cast<double*>(ws + 2 * p.x_bytes + p.part_bytes);
+    double* sc = reinterpret_cast<double*>(ws + 2 * p.x_bytes + p.part_bytes + p.np_bytes);
+    const int64_t n = h->n;
+    const int64_t vecs = n * (k / p.V);
+    const int ggrid = int(std::max<int64_t>(1, std::min<int64_t>((vecs + 255) / 256, int64_t(d.sm_count) * 16)));
+    cudaEvent_t e0 = pf.begin();
+    arrow_gather_rows_kernel<TX><<<ggrid, 256, 0, s>>>(static_cast<const TX*>(X), xa, d.iperm0, n, k, nullptr);
+    pf.end(ARROW_K_PERMUTE, e0);
+    TX* fin = xa;
+    switch (h->opts.value_dtype) {
+        case ARROW_F32: run_steps<TX, float>(h, p, xa, xb, k, iters, flags, part, np, sc, s, &fin, pf); break;
+        case ARROW_BF16: run_steps<TX, __nv_bfloat16>(h, p, xa, xb, k, iters, flags, part, np, sc, s, &fin, pf); break;
+        default: run_steps<TX, __half>(h, p, xa, xb, k, iters, flags, part, np, sc, s, &fin, pf); break;
+    }
+    const double* final_scale = (flags & ARROW_RESCALE) ? sc + (iters & 1) * k : nullptr;
+    e0 = pf.begin();
+    arrow_gather_rows_kernel<TX><<<ggrid, 256, 0, s>>>(fin, static_cast<TX*>(Y), d.perm0, n, k, final_scale);
+    pf.end(ARROW_K_PERMUTE, e0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "arrow_spmm: kernel launch");
+    return ARROW_OK;
+}
+
+static int check_spmm_args(const arrow_handle_s* h, const void* X, int64_t k, int32_t iters, void* Y, int32_t x_dtype,
+                           int32_t flags) {
+    if (!h) { set_error("arrow_spmm: NULL handle"); return ARROW_EINVAL; }
+    if (!h->uploaded) { set_error("arrow_spmm: handle is not uploaded (decomposed with ARROW_HOST_ONLY?)"); return ARROW_ESTATE; }
+    if (k < 0 || iters < 0) { set_error("arrow_spmm: k and iters must be >= 0"); return ARROW_EINVAL; }
+    if (!dtype_ok(x_dtype)) { set_error("arrow_spmm: unknown x_dtype"); return ARROW_EINVAL; }
+    if (flags & ~(ARROW_RESCALE | ARROW_PROFILE)) { set_error("arrow_spmm: unknown flags"); return ARROW_EINVAL; }
+    if (x_dtype == ARROW_F32 && h->opts.value_dtype != ARROW_F32) {
+        set_error("arrow_spmm: F32 features need F32 values");
+        return ARROW_EINVAL;
+    }
+    if (x_dtype != ARROW_F32 && h->opts.value_dtype != ARROW_F32 && h->opts.value_dtype != x_dtype) {
+        set_error("arrow_spmm: 16-bit features need values of the same type or F32");
+        return ARROW_EINVAL;
+    }
+    if (h->n > 0 && k > 0) {
+        if (!X || !Y) { set_error("arrow_spmm: X and Y must be non-NULL"); return ARROW_EINVAL; }
+        if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15) {
+            set_error("arrow_spmm: X and Y must be 16-byte aligned");
+            return ARROW_EINVAL;
+        }
+    }
+    return ARROW_OK;
+}
+
+static int spmm_dispatch(arrow_handle_s* h, const Plan& p, const void* X, int64_t k, int32_t iters, void* Y,
+                         int32_t x_dtype, int32_t flags, char* ws, cudaStream_t s) {
+    if (iters == 0) {
+        if (X != Y) ACK(cudaMemcpyAsync(Y, X, size_t(h->n) * size_t(k) * dtype_size(x_dtype), cudaMemcpyDeviceToDevice, s));
+        return ARROW_OK;
+    }
+    Prof pf;
+    if (flags & ARROW_PROFILE) { pf.h = h; pf.s = s; }
+    switch (x_dtype) {
+        case ARROW_F32: return spmm_typed<float>(h, p, X, k, iters, Y, flags, ws, s, pf);
+        case ARROW_BF16: return spmm_typed<__nv_bfloat16>(h, p, X, k, iters, Y, flags, ws, s, pf);
+        default: return spmm_typed<__half>(h, p, X, k, iters, Y, flags, ws, s, pf);
+    }
+}
+
+}  // namespace arrow
+
+// ======================================================================================
+// C-ABI
+// ======================================================================================
+using namespace arrow;
+
+extern "C" {
+
+const char* arrow_last_error(void) { return g_last_error.c_str(); }
+
+int arrow_opts_default(arrow_opts* o) {
+    if (!o) { set_error("arrow_opts_default: NULL"); return ARROW_EINVAL; }
+    std::memset(o, 0, sizeof(*o));
+    o->value_dtype = ARROW_F32;
+    o->predicate = ARROW_PRED_BLOCK;
+    o->device = -1;
+    return ARROW_OK;
+}
+
+int arrow_decompose(const arrow_csr* A, int64_t b, const arrow_opts* o, arrow_handle* out) {
+    if (!out) { set_error("arrow_decompose: out is NULL"); return ARROW_EINVAL; }
+    *out = nullptr;
+    arrow_opts opts;
+    if (o) opts = *o; else arrow_opts_default(&opts);
+    arrow_handle_s* h = nullptr;
+    try {
+        h = new arrow_handle_s();
+        int rc = decompose_host(h, A, b, opts);
+        if (rc != ARROW_OK) { delete h; return rc; }
+    } catch (const std::bad_alloc&) {
+        delete h;
+        set_error("arrow_decompose: host allocation failed");
+        return ARROW_ENOMEM;
+    }
+    if (!(opts.flags & ARROW_HOST_ONLY)) {
+        int rc = arrow_upload(h);
+        if (rc != ARROW_OK) { arrow_free(h); return rc; }
+    }
+    *out = h;
+    return ARROW_OK;
+}
+
+int arrow_upload(arrow_handle h) {
+    if (!h) { set_error("arrow_upload: NULL handle"); return ARROW_EINVAL; }
+    if (h->uploaded) return ARROW_OK;
+    if (h->opts.predicate != ARROW_PRED_BLOCK) {
+        set_error("arrow_upload: the device path needs the block-diagonal predicate");
+        return ARROW_EINVAL;
+    }
+    int rc;
+    try {
+        rc = upload_impl(h);
+    } catch (const std::bad_alloc&) {
+        set_error("arrow_upload: host allocation failed");
+        rc = ARROW_ENOMEM;
+    }
+    if (rc != ARROW_OK) { free_device(h->dev); return rc; }
+    h->uploaded = true;
+    return ARROW_OK;
+}
+
+void arrow_free(arrow_handle h) {
+    if (!h) return;
+    destroy_events(h);
+    if (h->uploaded || h->dev.rowptr || h->dev.ws) free_device(h->dev);
+    delete h;
+}
+
+int arrow_workspace_size(arrow_handle h, int64_t k, int32_t x_dtype, int32_t flags, size_t* bytes) {
+    if (!h || !bytes) { set_error("arrow_workspace_size: NULL argument"); return ARROW_EINVAL; }
+    if (!h->uploaded) { set_error("arrow_workspace_size: handle is not uploaded"); return ARROW_ESTATE; }
+    if (!dtype_ok(x_dtype) || k < 0) { set_error("arrow_workspace_size: bad k or dtype"); return ARROW_EINVAL; }
+    if (k == 0) { *bytes = 0; return ARROW_OK; }
+    Plan p;
+    int rc = make_plan(h, k, x_dtype, flags, p);
+    if (rc) return rc;
+    *bytes = p.total;
+    return ARROW_OK;
+}
+
+int arrow_spmm_ws(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y, int32_t x_dtype, int32_t flags,
+                  void* workspace, size_t ws_bytes, void* stream) {
+    int rc = check_spmm_args(h, X, k, iters, Y, x_dtype, flags);
+    if (rc) return rc;
+    if (h->n == 0 || k == 0) return ARROW_OK;
+    Plan p;
+    if ((rc = make_plan(h, k, x_dtype, flags, p))) return rc;
+    if (iters > 0 && (!workspace || ws_bytes < p.total || (reinterpret_cast<uintptr_t>(workspace) & 255))) {
+        set_error("arrow_spmm_ws: workspace missing, too small or not 256-byte aligned");
+        return ARROW_EINVAL;
+    }
+    return spmm_dispatch(h, p, X, k, iters, Y, x_dtype, flags, static_cast<char*>(workspace),
+                         static_cast<cudaStream_t>(stream));
+}
+
+int arrow_spmm(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y, int32_t x_dtype, int32_t flags,
+               void* stream) {
+    int rc = check_spmm_args(h, X, k, iters, Y, x_dtype, flags);
+    if (rc) return rc;
+    if (h->n == 0 || k == 0) return ARROW_OK;
+    Plan p;
+    if ((rc = make_plan(h, k, x_dtype, flags, p))) return rc;
+    if (iters > 0 && h->dev.ws_bytes < p.total) {
+        if (h->dev.ws) {
+            ACK(cudaDeviceSynchronize());
+            cudaFree(h->dev.ws);
+            h->dev.ws = nullptr;
+            h->dev.ws_bytes = 0;
+        }
+        ACK(cudaMalloc(&h->dev.ws, p.total));
+        h->dev.ws_bytes = p.total;
+    }
+    return spmm_dispatch(h, p, X, k, iters, Y, x_dtype, flags, static_cast<char*>(h->dev.ws),
+                         static_cast<cudaStream_t>(stream));
+}
+
+int arrow_num_levels(arrow_handle h, int32_t* l) {
+    if (!h || !l) { set_error("arrow_num_levels: NULL argument"); return ARROW_EINVAL; }
+    *l = int32_t(h->levels.size());
+    return ARROW_OK;
+}
+
+int arrow_level_info(arrow_handle h, int32_t i, int64_t* n_active, int64_t* nnz) {
+    if (!h || i < 0 || i >= int32_t(h->levels.size())) { set_error("arrow_level_info: bad handle or level"); return ARROW_EINVAL; }
+    if (n_active) *n_active = h->levels[i].n_active;
+    if (nnz) *nnz = h->levels[i].nnz;
+    return ARROW_OK;
+}
+
+int arrow_level_perm(arrow_handle h, int32_t i, int32_t* perm_out) {
+    if (!h || !perm_out || i < 0 || i >= int32_t(h->levels.size())) { set_error("arrow_level_perm: bad argument"); return ARROW_EINVAL; }
+    std::memcpy(perm_out, h->levels[i].perm.data(), size_t(h->n) * sizeof(int32_t));
+    return ARROW_OK;
+}
+
+int arrow_level_csr(arrow_handle h, int32_t i, int64_t* rowptr, int32_t* colidx, double* vals) {
+    if (!h || !rowptr || i < 0 || i >= int32_t(h->levels.size())) { set_error("arrow_level_csr: bad argument"); return ARROW_EINVAL; }
+    const int64_t n = h->n;
+    const int32_t* perm = h->levels[i].perm.data();
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t j = h->rowptr[r]; j < h->rowptr[r + 1]; ++j)
+            if (h->entry_level[j] == i) cnt[perm[r] + 1]++;
+    for (int64_t p = 0; p < n; ++p) cnt[p + 1] += cnt[p];
+    for (int64_t p = 0; p <= n; ++p) rowptr[p] = cnt[p];
+    if (cnt[n] == 0) return ARROW_OK;
+    if (!colidx || !vals) { set_error("arrow_level_csr: colidx/vals NULL"); return ARROW_EINVAL; }
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t j = h->rowptr[r]; j < h->rowptr[r + 1]; ++j)
+            if (h->entry_level[j] == i) {
+                int64_t o = fill[perm[r]]++;
+                colidx[o] = perm[h->colidx[j]];
+                vals[o] = h->values[j];
+            }
+    std::vector<std::pair<int32_t, double>> tmp;
+    for (int64_t p = 0; p < n; ++p) {
+        tmp.clear();
+        for (int64_t o = cnt[p]; o < cnt[p + 1]; ++o) tmp.push_back({colidx[o], vals[o]});
+        std::sort(tmp.begin(), tmp.end(), [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+            return a.first < b.first;
+        });
+        for (int64_t o = cnt[p]; o < cnt[p + 1]; ++o) { colidx[o] = tmp[o - cnt[p]].first; vals[o] = tmp[o - cnt[p]].second; }
+    }
+    return ARROW_OK;
+}
+
+int arrow_profile_get(arrow_handle h, int32_t kernel, double* total_ms, int64_t* launches) {
+    if (!h || !total_ms || !launches) { set_error("arrow_profile_get: NULL argument"); return ARROW_EINVAL; }
+    double ms = 0.0;
+    int64_t cnt = 0;
+    std::vector<ProfileRecord> keep;
+    for (auto& r : h->prof) {
+        if (r.kind != kernel) { keep.push_back(r); continue; }
+        cudaError_t e = cudaEventSynchronize(static_cast<cudaEvent_t>(r.stop));
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, static_cast<cudaEvent_t>(r.start), static_cast<cudaEvent_t>(r.stop));
+        if (e != cudaSuccess) return cuda_fail(e, "arrow_profile_get");
+        ms += t;
+        ++cnt;
+        h->event_pool.push_back(r.start);
+        h->event_pool.push_back(r.stop);
+    }
+    h->prof.swap(keep);
+    *total_ms = ms;
+    *launches = cnt;
+    return ARROW_OK;
+}
+
+int arrow_get_stats(arrow_handle h, arrow_stats* s) {
+    if (!h || !s) { set_error("arrow_get_stats: NULL argument"); return ARROW_EINVAL; }
+    s->n = h->n;
+    s->nnz = h->nnz;
+    s->b = h->b;
+    s->levels = int32_t(h->levels.size());
+    s->value_dtype = h->opts.value_dtype;
+    s->long_rows = int64_t(h->long_rows.size());
+    s->segments = int64_t(h->seg_begin.size());
+    s->device_bytes = int64_t(h->dev.bytes);
+    s->decompose_seconds = h->decompose_seconds;
+    return ARROW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,596 @@
+// Host side of the library: LA-Decompose (Section 4.1) with the random spanning forest
+// linear arrangement (Section 4.3) and the smallest-first tree layout (Section 4.4),
+// followed by the construction of the fused row program that the device kernels run.
+//
+// Readings of the paper taken here (the same ones the test oracle states):
+//   * positions are 0-based, the head is positions 0..b-1;
+//   * B_i uses the block-diagonal arrow shape of Section 3.1 / Fig. 2
+//     (r < b || c < b || r/b == c/b), or the band of Section 1 (|r-c| <= b) on request;
+//   * the graph of A_i is the symmetric pattern of its remaining entries without
+//     self-loops, deg(v) = number of distinct remaining neighbours;
+//   * head = the b vertices of largest degree, ties by smaller id, in that order;
+//   * the U(0,1) weights of Section 4.3 become distinct 64-bit keys
+//     w(u,v) = splitmix64(splitmix64(seed + i) ^ (u << 32 | v)), u < v (splitmix64 is a
+//     bijection, so the minimum spanning forest is unique);
+//   * trees in decreasing size; among single vertices those that still hold an entry
+//     (an edge to the head, or a diagonal entry) come first, so the touched rows of
+//     every level form a prefix (Section 3: non-zero rows collected at the top); then
+//     smallest vertex id; each tree is rooted at its smallest id; siblings in
+//     increasing subtree size, ties by id;
+//   * levels are built until no entry is left.
+//
+// The minimum spanning forest is computed with a parallel Boruvka (a component's
+// lightest edge is in the unique forest), which agrees with Kruskal because keys are
+// distinct.  The arrangement of a tree is computed top-down: a child's position is its
+// parent's position + 1 + the sizes of its smaller siblings, which is the smallest-first
+// preorder written without recursion.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+#include <thread>
+#include <utility>
+
+#include "arrow_internal.h"
+
+namespace arrow {
+namespace {
+
+int g_threads = 1;
+
+// f(begin, end, thread) over [0, n) in g_threads contiguous chunks.
+template <class F>
+void pfor(int64_t n, F&& f) {
+    int T = g_threads;
+    if (n < 32768 || T <= 1) {
+        if (n > 0) f(int64_t(0), n, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(T);
+    for (int t = 0; t < T; ++t) {
+        int64_t b = n * t / T, e = n * (t + 1) / T;
+        th.emplace_back([&f, b, e, t] { f(b, e, t); });
+    }
+    for (auto& x : th) x.join();
+}
+
+// Order-preserving parallel filter: out receives emit(i) for every i with keep(i).
+template <class T, class Keep, class Emit>
+void pfilter(int64_t n, std::vector<T>& out, Keep&& keep, Emit&& emit) {
+    int T_ = (n < 32768) ? 1 : g_threads;
+    std::vector<int64_t> cnt(T_ + 1, 0);
+    auto count = [&](int64_t b, int64_t e, int t) {
+        int64_t c = 0;
+        for (int64_t i = b; i < e; ++i) c += keep(i) ? 1 : 0;
+        cnt[t + 1] = c;
+    };
+    if (T_ == 1) count(0, n, 0); else pfor(n, count);
+    for (int t = 0; t < T_; ++t) cnt[t + 1] += cnt[t];
+    out.resize(cnt[T_]);
+    auto fill = [&](int64_t b, int64_t e, int t) {
+        int64_t o = cnt[t];
+        for (int64_t i = b; i < e; ++i)
+            if (keep(i)) out[o++] = emit(i);
+    };
+    if (T_ == 1) fill(0, n, 0); else pfor(n, fill);
+}
+
+inline uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <class T>
+inline void atomic_min_relaxed(T& slot, T v) {
+    std::atomic_ref<T> a(slot);
+    T cur = a.load(std::memory_order_relaxed);
+    while (v < cur && !a.compare_exchange_weak(cur, v, std::memory_order_relaxed)) {
+    }
+}
+
+template <class T>
+inline T aload(T& slot) { return std::atomic_ref<T>(slot).load(std::memory_order_relaxed); }
+template <class T>
+inline void astore(T& slot, T v) { std::atomic_ref<T>(slot).store(v, std::memory_order_relaxed); }
+
+inline bool pred_block(int64_t r, int64_t c, int64_t b) { return r < b || c < b || (r / b) == (c / b); }
+inline bool pred_band(int64_t r, int64_t c, int64_t b) {
+    return r < b || c < b || (r > c ? r - c : c - r) <= b;
+}
+
+struct Ent {
+    int32_t r, c;  // vertices
+    int32_t s;     // index of the entry in the symmetric pattern
+};
+
+int validate(const arrow_csr* A) {
+    if (!A) { set_error("arrow_decompose: A is NULL"); return ARROW_EINVAL; }
+    if (A->n < 0 || A->n >= (int64_t(1) << 31)) { set_error("arrow_decompose: n out of range [0, 2^31)"); return ARROW_EINVAL; }
+    if (A->nnz < 0 || A->nnz >= (int64_t(1) << 31)) { set_error("arrow_decompose: nnz out of range [0, 2^31)"); return ARROW_EINVAL; }
+    if (A->n > 0 && !A->rowptr) { set_error("arrow_decompose: rowptr is NULL"); return ARROW_EINVAL; }
+    if (A->nnz > 0 && (!A->colidx || !A->values)) { set_error("arrow_decompose: colidx/values NULL"); return ARROW_EINVAL; }
+    if (A->n == 0) {
+        if (A->nnz != 0) { set_error("arrow_decompose: nnz > 0 with n == 0"); return ARROW_EINVAL; }
+        return ARROW_OK;
+    }
+    if (A->rowptr[0] != 0 || A->rowptr[A->n] != A->nnz) {
+        set_error("arrow_decompose: rowptr[0] must be 0 and rowptr[n] must be nnz");
+        return ARROW_EINVAL;
+    }
+    std::atomic<int> bad{0};
+    pfor(A->n, [&](int64_t b, int64_t e, int) {
+        for (int64_t r = b; r < e; ++r) {
+            int64_t s = A->rowptr[r], t = A->rowptr[r + 1];
+            if (t < s || s < 0 || t > A->nnz) { bad.store(1); return; }
+            int64_t prev = -1;
+            for (int64_t j = s; j < t; ++j) {
+                int64_t c = A->colidx[j];
+                if (c < 0 || c >= A->n) { bad.store(2); return; }
+                if (c <= prev) { bad.store(3); return; }
+                prev = c;
+            }
+        }
+    });
+    switch (bad.load()) {
+        case 1: set_error("arrow_decompose: rowptr is not non-decreasing within [0, nnz]"); return ARROW_EINVAL;
+        case 2: set_error("arrow_decompose: column index out of range"); return ARROW_EINVAL;
+        case 3: set_error("arrow_decompose: column indices must be strictly increasing in each row"); return ARROW_EINVAL;
+        default: return ARROW_OK;
+    }
+}
+
+// Symmetric pattern S = pattern(A) U pattern(A^T).  If A is already structurally
+// symmetric S is A's pattern (a2s empty = identity).
+struct SymPattern {
+    const int64_t* ptr = nullptr;
+    const int32_t* col = nullptr;
+    int64_t nnz = 0;
+    std::vector<int64_t> own_ptr;
+    std::vector<int32_t> own_col;
+    std::vector<int32_t> a2s;  // A entry -> S entry (empty when identity)
+};
+
+bool row_has(const int64_t* ptr, const int32_t* col, int64_t r, int32_t c) {
+    const int32_t* b = col + ptr[r];
+    const int32_t* e = col + ptr[r + 1];
+    const int32_t* it = std::lower_bound(b, e, c);
+    return it != e && *it == c;
+}
+
+void build_sym(const arrow_csr* A, SymPattern& S) {
+    const int64_t n = A->n;
+    std::atomic<bool> sym{true};
+    pfor(n, [&](int64_t b, int64_t e, int) {
+        for (int64_t r = b; r < e && sym.load(std::memory_order_relaxed); ++r)
+            for (int64_t j = A->rowptr[r]; j < A->rowptr[r + 1]; ++j)
+                if (!row_has(A->rowptr, A->colidx, A->colidx[j], int32_t(r))) { sym.store(false); return; }
+    });
+    if (sym.load()) {
+        S.ptr = A->rowptr;
+        S.col = A->colidx;
+        S.nnz = A->nnz;
+        return;
+    }
+    // transpose pattern (rows ascending inside each column list)
+    std::vector<int64_t> tptr(n + 1, 0);
+    for (int64_t j = 0; j < A->nnz; ++j) tptr[A->colidx[j] + 1]++;
+    for (int64_t i = 0; i < n; ++i) tptr[i + 1] += tptr[i];
+    std::vector<int32_t> tcol(A->nnz);
+    {
+        std::vector<int64_t> pos(tptr.begin(), tptr.end() - 1);
+        for (int64_t r = 0; r < n; ++r)
+            for (int64_t j = A->rowptr[r]; j < A->rowptr[r + 1]; ++j) tcol[pos[A->colidx[j]]++] = int32_t(r);
+    }
+    // merge row r of A with row r of A^T
+    S.own_ptr.assign(n + 1, 0);
+    for (int64_t r = 0; r < n; ++r) {
+        int64_t a = A->rowptr[r], ae = A->rowptr[r + 1], t = tptr[r], te = tptr[r + 1], m = 0;
+        while (a < ae || t < te) {
+            if (t >= te || (a < ae && A->colidx[a] < tcol[t])) ++a;
+            else if (a >= ae || tcol[t] < A->colidx[a]) ++t;
+            else { ++a; ++t; }
+            ++m;
+        }
+        S.own_ptr[r + 1] = S.own_ptr[r] + m;
+    }
+    S.nnz = S.own_ptr[n];
+    S.own_col.resize(S.nnz);
+    S.a2s.resize(A->nnz);
+    for (int64_t r = 0; r < n; ++r) {
+        int64_t a = A->rowptr[r], ae = A->rowptr[r + 1], t = tptr[r], te = tptr[r + 1], o = S.own_ptr[r];
+        while (a < ae || t < te) {
+            if (t >= te || (a < ae && A->colidx[a] < tcol[t])) { S.a2s[a] = int32_t(o); S.own_col[o++] = A->colidx[a++]; }
+            else if (a >= ae || tcol[t] < A->colidx[a]) { S.own_col[o++] = tcol[t++]; }
+            else { S.a2s[a] = int32_t(o); S.own_col[o++] = A->colidx[a++]; ++t; }
+        }
+    }
+    S.ptr = S.own_ptr.data();
+    S.col = S.own_col.data();
+}
+
+// Step 1 of LA-Decompose: min(b, n) vertices by (degree desc, id asc).
+std::vector<int32_t> select_head(const std::vector<int32_t>& deg, int64_t b) {
+    const int64_t n = int64_t(deg.size());
+    const int64_t hb = std::min<int64_t>(b, n);
+    int32_t maxdeg = 0;
+    for (int64_t v = 0; v < n; ++v) maxdeg = std::max(maxdeg, deg[v]);
+    std::vector<int64_t> cnt(size_t(maxdeg) + 2, 0);
+    for (int64_t v = 0; v < n; ++v) cnt[deg[v]]++;
+    // threshold D: #(deg > D) < hb <= #(deg >= D)
+    int64_t above = 0;
+    int32_t D = maxdeg;
+    for (;; --D) {
+        if (above + cnt[D] >= hb || D == 0) break;
+        above += cnt[D];
+    }
+    std::vector<int32_t> head;
+    head.reserve(hb);
+    for (int64_t v = 0; v < n; ++v)
+        if (deg[v] > D) head.push_back(int32_t(v));
+    std::sort(head.begin(), head.end(), [&](int32_t x, int32_t y) {
+        return deg[x] != deg[y] ? deg[x] > deg[y] : x < y;
+    });
+    for (int64_t v = 0; v < n && int64_t(head.size()) < hb; ++v)
+        if (deg[v] == D) head.push_back(int32_t(v));
+    return head;
+}
+
+// Minimum spanning forest of the edge set (unique keys) by parallel Boruvka.
+// On return comp[v] is the representative of v's tree (every vertex, isolated ones
+// are their own representative) and `forest` holds the forest edges (any order).
+void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::vector<uint64_t> ew,
+             std::vector<int32_t>& comp, std::vector<std::pair<int32_t, int32_t>>& forest) {
+    comp.resize(n);
+    std::iota(comp.begin(), comp.end(), 0);
+    std::vector<uint64_t> best(n);
+    std::vector<int32_t> link(n);
+    std::vector<int32_t> stamp(n, -1);
+    forest.assign(std::min<int64_t>(n, int64_t(eu.size())), {0, 0});
+    std::atomic<int64_t> fcount{0};
+    const uint64_t NONE = ~uint64_t(0);
+    int round = 0;
+    while (!eu.empty()) {
+        const int64_t m = int64_t(eu.size());
+        pfor(m, [&](int64_t b, int64_t e, int) {
+            for (int64_t i = b; i < e; ++i) {
+                int32_t cu = comp[eu[i]], cv = comp[ev[i]];
+                astore(best[cu], NONE); astore(best[cv], NONE);
+                astore(link[cu], cu); astore(link[cv], cv);
+                astore(stamp[cu], round); astore(stamp[cv], round);
+            }
+        });
+        pfor(m, [&](int64_t b, int64_t e, int) {
+            for (int64_t i = b; i < e; ++i) {
+                int32_t cu = comp[eu[i]], cv = comp[ev[i]];
+                if (cu == cv) continue;
+                atomic_min_relaxed(best[cu], ew[i]);
+                atomic_min_relaxed(best[cv], ew[i]);
+            }
+        });
+        std::atomic<int64_t> selected{0};
+        pfor(m, [&](int64_t b, int64_t e, int) {
+            int64_t sel = 0;
+            for (int64_t i = b; i < e; ++i) {
+                int32_t cu = comp[eu[i]], cv = comp[ev[i]];
+                if (cu == cv) continue;
+                bool a = aload(best[cu]) == ew[i], c = aload(best[cv]) == ew[i];
+                if (!a && !c) continue;
+                forest[fcount.fetch_add(1, std::memory_order_relaxed)] = {eu[i], ev[i]};
+                if (a) astore(link[cu], cv);
+                if (c) astore(link[cv], cu);
+                ++sel;
+            }
+            selected.fetch_add(sel);
+        });
+        if (selected.load() == 0) break;
+        // mutual choices form 2-cycles: the smaller label becomes the root
+        pfor(m, [&](int64_t b, int64_t e, int) {
+            for (int64_t i = b; i < e; ++i) {
+                for (int32_t c : {comp[eu[i]], comp[ev[i]]}) {
+                    int32_t l = aload(link[c]);
+                    if (l != c && aload(link[l]) == c && c < l) astore(link[c], c);
+                }
+            }
+        });
+        // pointer jumping to the roots
+        pfor(m, [&](int64_t b, int64_t e, int) {
+            for (int64_t i = b; i < e; ++i) {
+                for (int32_t c : {comp[eu[i]], comp[ev[i]]}) {
+                    for (;;) {
+                        int32_t l = aload(link[c]);
+                        int32_t ll = aload(link[l]);
+                        if (l == ll) break;
+                        astore(link[c], ll);
+                    }
+                }
+            }
+        });
+        pfor(n, [&](int64_t b, int64_t e, int) {
+            for (int64_t v = b; v < e; ++v) {
+                int32_t c = comp[v];
+                if (stamp[c] == round) {
+                    int32_t r = c;
+                    for (;;) { int32_t l = link[r]; if (l == r) break; r = l; }
+                    comp[v] = r;
+                }
+            }
+        });
+        // drop edges inside one component
+        std::vector<int32_t> nu, nv;
+        std::vector<uint64_t> nw;
+        std::vector<int64_t> keep_idx;
+        pfilter(m, keep_idx, [&](int64_t i) { return comp[eu[i]] != comp[ev[i]]; },
+                [&](int64_t i) { return i; });
+        nu.resize(keep_idx.size()); nv.resize(keep_idx.size()); nw.resize(keep_idx.size());
+        pfor(int64_t(keep_idx.size()), [&](int64_t b, int64_t e, int) {
+            for (int64_t j = b; j < e; ++j) { nu[j] = eu[keep_idx[j]]; nv[j] = ev[keep_idx[j]]; nw[j] = ew[keep_idx[j]]; }
+        });
+        eu.swap(nu); ev.swap(nv); ew.swap(nw);
+        ++round;
+    }
+    forest.resize(fcount.load());
+}
+
+// Sections 4.3 step 3 and 4.4: trees in decreasing size, each in smallest-first order,
+// after the head.  Writes perm (vertex -> position) and iperm.
+void arrange(int64_t n, const std::vector<int32_t>& head, const std::vector<uint8_t>& is_head,
+             const std::vector<uint8_t>& touched, const std::vector<int32_t>& comp, const std::vector<std::pair<int32_t, int32_t>>& forest,
+             std::vector<int32_t>& perm, std::vector<int32_t>& iperm) {
+    const int64_t hb = int64_t(head.size());
+    perm.assign(n, -1);
+    iperm.assign(n, -1);
+    for (int64_t p = 0; p < hb; ++p) { perm[head[p]] = int32_t(p); iperm[p] = head[p]; }
+
+    // tree sizes and smallest ids, keyed by representative
+    std::vector<int32_t> tsize(n, 0), tmin(n, INT32_MAX);
+    pfor(n, [&](int64_t b, int64_t e, int) {
+        for (int64_t v = b; v < e; ++v) {
+            if (is_head[v]) continue;
+            std::atomic_ref<int32_t>(tsize[comp[v]]).fetch_add(1, std::memory_order_relaxed);
+            atomic_min_relaxed(tmin[comp[v]], int32_t(v));
+        }
+    });
+    struct Tree { int32_t size, root; int64_t start; };
+    std::vector<Tree> multi;
+    for (int64_t v = 0; v < n; ++v)
+        if (!is_head[v] && comp[v] == v && tsize[v] >= 2) multi.push_back({tsize[v], tmin[v], 0});
+    std::sort(multi.begin(), multi.end(), [](const Tree& x, const Tree& y) {
+        return x.size != y.size ? x.size > y.size : x.root < y.root;
+    });
+    int64_t pos = hb;
+    for (auto& t : multi) { t.start = pos; pos += t.size; }
+    // single vertices: those holding an entry first, each group in id order
+    for (int pass = 0; pass < 2; ++pass)
+        for (int64_t v = 0; v < n; ++v)
+            if (!is_head[v] && tsize[comp[v]] == 1 && (touched[v] != 0) == (pass == 0)) {
+                perm[v] = int32_t(pos); iperm[pos] = int32_t(v); ++pos;
+            }
+
+    // forest adjacency
+    std::vector<int64_t> fptr(n + 1, 0);
+    for (auto& e : forest) { fptr[e.first + 1]++; fptr[e.second + 1]++; }
+    for (int64_t v = 0; v < n; ++v) fptr[v + 1] += fptr[v];
+    std::vector<int32_t> fadj(fptr[n]);
+    {
+        std::vector<int64_t> fill(fptr.begin(), fptr.end() - 1);
+        for (auto& e : forest) { fadj[fill[e.first]++] = e.second; fadj[fill[e.second]++] = e.first; }
+    }
+    std::vector<int32_t> parent(n, -1), sub(n, 0);
+    std::atomic<int64_t> next{0};
+    auto worker = [&] {
+        std::vector<int32_t> order;
+        std::vector<int32_t> kids;
+        for (;;) {
+            int64_t ti = next.fetch_add(1);
+            if (ti >= int64_t(multi.size())) return;
+            const Tree& t = multi[ti];
+            order.clear();
+            order.push_back(t.root);
+            parent[t.root] = -1;
+            for (size_t q = 0; q < order.size(); ++q) {
+                int32_t v = order[q];
+                for (int64_t j = fptr[v]; j < fptr[v + 1]; ++j) {
+                    int32_t u = fadj[j];
+                    if (u == parent[v]) continue;
+                    parent[u] = v;
+                    order.push_back(u);
+                }
+            }
+            for (int32_t v : order) sub[v] = 1;
+            for (size_t q = order.size(); q-- > 1;) sub[parent[order[q]]] += sub[order[q]];
+            perm[t.root] = int32_t(t.start);
+            for (int32_t v : order) {
+                kids.clear();
+                for (int64_t j = fptr[v]; j < fptr[v + 1]; ++j)
+                    if (fadj[j] != parent[v]) kids.push_back(fadj[j]);
+                std::sort(kids.begin(), kids.end(), [&](int32_t x, int32_t y) {
+                    return sub[x] != sub[y] ? sub[x] < sub[y] : x < y;
+                });
+                int64_t run = int64_t(perm[v]) + 1;
+                for (int32_t u : kids) { perm[u] = int32_t(run); run += sub[u]; }
+            }
+            for (int32_t v : order) iperm[perm[v]] = v;
+        }
+    };
+    int T = std::max(1, std::min<int>(g_threads, int(multi.size())));
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t) th.emplace_back(worker);
+    for (auto& x : th) x.join();
+}
+
+}  // namespace
+
+int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow_opts& o) {
+    auto t0 = std::chrono::steady_clock::now();
+    g_threads = o.nthreads > 0 ? o.nthreads : int(std::max(1u, std::thread::hardware_concurrency()));
+    g_threads = std::min(g_threads, 256);
+    if (b < 2) { set_error("arrow_decompose: b must be >= 2 (Section 4.1)"); return ARROW_EINVAL; }
+    if (o.predicate != ARROW_PRED_BLOCK && o.predicate != ARROW_PRED_BAND) {
+        set_error("arrow_decompose: unknown predicate");
+        return ARROW_EINVAL;
+    }
+    if (o.value_dtype < ARROW_F32 || o.value_dtype > ARROW_F16) {
+        set_error("arrow_decompose: unknown value_dtype");
+        return ARROW_EINVAL;
+    }
+    int rc = validate(A);
+    if (rc != ARROW_OK) return rc;
+    const int64_t n = A->n, nnz = A->nnz;
+    const int max_levels = o.max_levels > 0 ? std::min(o.max_levels, 254) : 254;
+    h->n = n; h->nnz = nnz; h->b = b; h->opts = o;
+    h->rowptr.assign(A->rowptr, A->rowptr + n + 1);
+    h->colidx.assign(A->colidx, A->colidx + nnz);
+    h->values.assign(A->values, A->values + nnz);
+
+    SymPattern S;
+    build_sym(A, S);
+    if (S.nnz >= (int64_t(1) << 31)) { set_error("arrow_decompose: symmetric pattern too large"); return ARROW_EINVAL; }
+
+    std::vector<uint8_t> lvlS(S.nnz, 255);
+    std::vector<Ent> act(S.nnz);
+    pfor(n, [&](int64_t bb, int64_t e, int) {
+        for (int64_t r = bb; r < e; ++r)
+            for (int64_t j = S.ptr[r]; j < S.ptr[r + 1]; ++j) act[j] = {int32_t(r), S.col[j], int32_t(j)};
+    });
+    const bool band = o.predicate == ARROW_PRED_BAND;
+    std::vector<int32_t> deg(n);
+    std::vector<uint8_t> is_head(n), touched(n);
+    int level = 0;
+    while (!act.empty()) {
+        if (level >= max_levels) {
+            set_error("arrow_decompose: more than max_levels levels");
+            return ARROW_EINVAL;
+        }
+        std::fill(deg.begin(), deg.end(), 0);
+        std::fill(touched.begin(), touched.end(), 0);
+        pfor(int64_t(act.size()), [&](int64_t bb, int64_t e, int) {
+            for (int64_t i = bb; i < e; ++i) {
+                astore(touched[act[i].r], uint8_t(1));   // S is symmetric: rows cover columns
+                if (act[i].r != act[i].c)
+                    std::atomic_ref<int32_t>(deg[act[i].r]).fetch_add(1, std::memory_order_relaxed);
+            }
+        });
+        std::vector<int32_t> head = select_head(deg, b);
+        std::fill(is_head.begin(), is_head.end(), 0);
+        for (int32_t v : head) is_head[v] = 1;
+
+        // edges of G_i' = G_i[V \ V^h], keyed by the level's random weights
+        const uint64_t salt = splitmix64(o.seed + uint64_t(level));
+        std::vector<int32_t> eu, ev;
+        std::vector<uint64_t> ew;
+        {
+            std::vector<int64_t> idx;
+            pfilter(int64_t(act.size()), idx,
+                    [&](int64_t i) { const Ent& x = act[i]; return x.r < x.c && !is_head[x.r] && !is_head[x.c]; },
+                    [&](int64_t i) { return i; });
+            eu.resize(idx.size()); ev.resize(idx.size()); ew.resize(idx.size());
+            pfor(int64_t(idx.size()), [&](int64_t bb, int64_t e, int) {
+                for (int64_t j = bb; j < e; ++j) {
+                    const Ent& x = act[idx[j]];
+                    eu[j] = x.r; ev[j] = x.c;
+                    ew[j] = splitmix64(salt ^ ((uint64_t(uint32_t(x.r)) << 32) | uint64_t(uint32_t(x.c))));
+                }
+            });
+        }
+        std::vector<int32_t> comp;
+        std::vector<std::pair<int32_t, int32_t>> forest;
+        boruvka(n, std::move(eu), std::move(ev), std::move(ew), comp, forest);
+        Level L;
+        std::vector<int32_t> iperm;
+        arrange(n, head, is_head, touched, comp, forest, L.perm, iperm);
+
+        // steps 3-4: entries inside the arrow shape go to B_i, the rest stays
+        const int32_t* perm = L.perm.data();
+        std::vector<Ent> rest;
+        pfilter(int64_t(act.size()), rest,
+                [&](int64_t i) {
+                    const Ent& x = act[i];
+                    int64_t p = perm[x.r], q = perm[x.c];
+                    bool take = band ? pred_band(p, q, b) : pred_block(p, q, b);
+                    if (take) lvlS[x.s] = uint8_t(level);
+                    return !take;
+                },
+                [&](int64_t i) { return act[i]; });
+        act.swap(rest);
+        h->levels.push_back(std::move(L));
+        ++level;
+    }
+    // level of every entry of A, per-level nnz and active rows
+    h->entry_level.resize(nnz);
+    const int nl = int(h->levels.size());
+    std::vector<std::vector<int64_t>> cnt(g_threads, std::vector<int64_t>(nl, 0));
+    std::vector<std::vector<int64_t>> mx(g_threads, std::vector<int64_t>(nl, -1));
+    pfor(n, [&](int64_t bb, int64_t e, int t) {
+        for (int64_t r = bb; r < e; ++r)
+            for (int64_t j = A->rowptr[r]; j < A->rowptr[r + 1]; ++j) {
+                uint8_t l = S.a2s.empty() ? lvlS[j] : lvlS[S.a2s[j]];
+                h->entry_level[j] = l;
+                const int32_t* p = h->levels[l].perm.data();
+                cnt[t][l]++;
+                mx[t][l] = std::max<int64_t>(mx[t][l], std::max(p[r], p[A->colidx[j]]));
+            }
+    });
+    for (int l = 0; l < nl; ++l) {
+        int64_t c = 0, m = -1;
+        for (int t = 0; t < g_threads; ++t) { c += cnt[t][l]; m = std::max(m, mx[t][l]); }
+        h->levels[l].nnz = c;
+        h->levels[l].n_active = m + 1;
+    }
+
+    // Fused row program: row p of pi_0 holds the entries of vertex v = pi_0^{-1}(p) of
+    // every level, in level order, inside a level in increasing level position of the
+    // column (the CSR order of B_i).  Each entry reads X row pi_0(column vertex).
+    if (!band) {
+        std::vector<int32_t> iperm0(n);
+        const int32_t* perm0 = nl ? h->levels[0].perm.data() : nullptr;
+        if (nl) for (int64_t v = 0; v < n; ++v) iperm0[perm0[v]] = int32_t(v);
+        else std::iota(iperm0.begin(), iperm0.end(), 0);
+        h->f_rowptr.assign(n + 1, 0);
+        for (int64_t p = 0; p < n; ++p) {
+            int32_t v = iperm0[p];
+            h->f_rowptr[p + 1] = h->f_rowptr[p] + int32_t(A->rowptr[v + 1] - A->rowptr[v]);
+        }
+        h->f_col.resize(nnz);
+        h->f_src.resize(nnz);
+        pfor(n, [&](int64_t bb, int64_t e, int) {
+            std::vector<std::pair<uint64_t, int32_t>> tmp;
+            for (int64_t p = bb; p < e; ++p) {
+                int32_t v = iperm0[p];
+                tmp.clear();
+                for (int64_t j = A->rowptr[v]; j < A->rowptr[v + 1]; ++j) {
+                    uint8_t l = h->entry_level[j];
+                    uint64_t key = (uint64_t(l) << 32) | uint32_t(h->levels[l].perm[A->colidx[j]]);
+                    tmp.push_back({key, int32_t(j)});
+                }
+                std::sort(tmp.begin(), tmp.end());
+                int64_t o = h->f_rowptr[p];
+                for (auto& x : tmp) {
+                    h->f_col[o] = perm0[A->colidx[x.second]];
+                    h->f_src[o] = x.second;
+                    ++o;
+                }
+            }
+        });
+        const int32_t long_row = o.long_row > 0 ? o.long_row : 64;
+        const int32_t seg = o.segment > 0 ? o.segment : 512;
+        h->long_rows.clear(); h->long_segptr.assign(1, 0); h->seg_begin.clear(); h->seg_end.clear();
+        for (int64_t p = 0; p < n; ++p) {
+            int32_t s = h->f_rowptr[p], e = h->f_rowptr[p + 1];
+            if (e - s <= long_row) continue;
+            h->long_rows.push_back(int32_t(p));
+            for (int32_t j = s; j < e; j += seg) {
+                h->seg_begin.push_back(j);
+                h->seg_end.push_back(std::min(e, j + seg));
+            }
+            h->long_segptr.push_back(int32_t(h->seg_begin.size()));
+        }
+    }
+    h->decompose_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return ARROW_OK;
+}
+
+}  // namespace arrow

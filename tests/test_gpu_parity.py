@@ -1,0 +1,215 @@
+"""GPU parity: arrow_spmm (through the C-ABI) against the FP64 oracle.
+
+Tolerances (stated per dtype, the accuracy bar of the arrow-SpMM workloads):
+  * FP32 values and features: max over columns j of
+        ||y_j - y_ref,j||_inf / ||y_ref,j||_inf  <=  1e-5 * iters
+  * BF16 / FP16 storage, FP32 accumulation: max_j ||y_j - y_ref,j||_2 / ||y_ref,j||_2 <= 2e-2
+The oracle is the plain FP64 product iterated (Eq. 1 is an identity), run on
+the same seeded inputs; no expected value comes from the GPU.
+"""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import spmm as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def arrow():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_19364_gb300 import build
+    build.build()
+    import paper_2402_19364_gb300 as pkg
+    return pkg
+
+
+TORCH_DT = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+
+
+def err_inf(Y, R):
+    return float(np.max(np.max(np.abs(Y - R), axis=0) / np.max(np.abs(R), axis=0)))
+
+
+def err_2(Y, R):
+    return float(np.max(np.linalg.norm(Y - R, axis=0) / np.linalg.norm(R, axis=0)))
+
+
+def run(arrow, A, b, X, iters, dt="f32", vdt=None, rescale=False, **kw):
+    M = arrow.ArrowMatrix(A, b, value_dtype=vdt or dt, **kw)
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to("cuda", TORCH_DT[dt])
+    Y = M.spmm(Xd, iters, rescale=rescale)
+    torch.cuda.synchronize()
+    return M, Xd, Y.float().cpu().numpy().astype(np.float64)
+
+
+def test_grid2d_64_fp32_ten_iterations(arrow):
+    # 2D 64x64 grid, 5-point stencil, U(0.5,1.5) row-normalised f32, b = 64, X 4096x16 N(0,1), 10 iterations
+    A = w.grid2d_64(seed=1)
+    X = w.features(A.n, 16, seed=2)
+    M, _, Y = run(arrow, A, 64, X, 10)
+    assert M.num_levels >= 2
+    assert err_inf(Y, S.iterate(A, X, 10)) <= 1e-5 * 10
+
+
+def test_grid3d_rescale_fp64_norms(arrow):
+    # 3D 7-point grid with the per-iteration FP64 column-norm rescale (scaled-down 400^3 workload)
+    A = w.grid3d(24, seed=3)
+    X = w.features(A.n, 16, seed=4)
+    _, _, Y = run(arrow, A, 96, X, 20, rescale=True)
+    R = S.iterate(A, X, 20, rescale=True)
+    assert err_inf(Y, R) <= 1e-5 * 20
+    assert np.allclose(np.linalg.norm(Y, axis=0), 1.0, atol=1e-5)
+
+
+@pytest.mark.parametrize("dt,k", [("f32", 4), ("f32", 8), ("f32", 16), ("f32", 32), ("f32", 64), ("f32", 128),
+                                  ("f32", 256), ("bf16", 8), ("bf16", 16), ("bf16", 64), ("bf16", 128),
+                                  ("bf16", 512), ("f16", 8), ("f16", 32), ("f16", 256)])
+def test_power_law_split_rows_all_widths(arrow, dt, k):
+    # R-MAT GCN matrix; long_row / segment small so head rows and many band rows are split
+    A = w.rmat_gcn(11, 16, seed=5)
+    X = w.features(A.n, k, seed=6)
+    iters = 4
+    M, _, Y = run(arrow, A, 64, X, iters, dt=dt, long_row=16, segment=32)
+    assert M.stats()["segments"] > 0
+    R = S.iterate(A, X, iters)
+    if dt == "f32":
+        assert err_inf(Y, R) <= 1e-5 * iters
+    else:
+        assert err_2(Y, R) <= 2e-2
+
+
+def test_bf16_values_against_fp32_and_fp64(arrow):
+    # power-law workload: BF16 A and X with FP32 accumulation vs the FP32 path and the FP64 oracle
+    A = w.rmat_gcn(13, 16, seed=5)
+    X = w.features(A.n, 128, seed=6)
+    iters = 8
+    R = S.iterate(A, X, iters)
+    _, _, Yb = run(arrow, A, 256, X, iters, dt="bf16")
+    _, _, Yf = run(arrow, A, 256, X, iters, dt="f32")
+    assert err_inf(Yf, R) <= 1e-5 * iters
+    assert err_2(Yb, R) <= 2e-2
+    assert err_2(Yb, Yf) <= 2e-2
+    # bf16 features with f32 values
+    _, _, Ym = run(arrow, A, 256, X, iters, dt="bf16", vdt="f32")
+    assert err_2(Ym, R) <= 2e-2
+
+
+@pytest.mark.parametrize("k", [8, 16, 32, 64])
+def test_rgg_fp16(arrow, k):
+    A = w.rgg(6000, seed=7)
+    b = int(np.ceil(np.sqrt(A.n)))
+    X = w.features(A.n, k, seed=8)
+    _, _, Y = run(arrow, A, b, X, 10, dt="f16")
+    assert err_2(Y, S.iterate(A, X, 10)) <= 2e-2
+
+
+def test_iters_zero_alias_and_determinism(arrow):
+    A = w.grid_stencil((37, 29), seed=9)            # ragged: n = 1073 is not a multiple of b
+    X = w.features(A.n, 32, seed=10)
+    M = arrow.ArrowMatrix(A, 16)
+    Xd = torch.from_numpy(X).cuda()
+    Y0 = M.spmm(Xd, 0)
+    assert torch.equal(Y0, Xd)
+    Y1 = M.spmm(Xd, 7)
+    Y2 = M.spmm(Xd, 7)
+    torch.cuda.synchronize()
+    assert torch.equal(Y1, Y2)                       # fixed accumulation order: bit-identical
+    Xa = Xd.clone()
+    M.spmm(Xa, 7, out=Xa)                            # X and Y may alias
+    assert torch.equal(Xa, Y1)
+    ws = torch.empty(M.workspace_size(32, "f32"), dtype=torch.uint8, device="cuda")
+    Y3 = M.spmm_ws(Xd, 7, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(Y3, Y1)
+    assert err_inf(Y1.cpu().numpy().astype(np.float64), S.iterate(A, X, 7)) <= 7e-5
+
+
+def test_empty_and_single_level(arrow):
+    n = 640
+    A0 = w.Csr(n, np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    M = arrow.ArrowMatrix(A0, 8)
+    Xd = torch.randn(n, 16, device="cuda")
+    assert torch.count_nonzero(M.spmm(Xd, 3)).item() == 0
+    A = w.random_csr(300, 0.02, 3, symmetric=True, diag=True)
+    X = w.features(A.n, 16, seed=1)
+    M, _, Y = run(arrow, A, 512, X, 5)               # b >= n: one level, all rows are head rows
+    assert M.num_levels == 1
+    assert err_inf(Y, S.iterate(A, X, 5)) <= 5e-5
+
+
+def test_nonsymmetric_matrix(arrow):
+    A = w.random_csr(2000, 0.002, 11)
+    X = w.features(A.n, 16, seed=3)
+    _, _, Y = run(arrow, A, 32, X, 3)
+    assert err_inf(Y, S.iterate(A, X, 3)) <= 3e-5
+
+
+def test_argument_errors(arrow):
+    from paper_2402_19364_gb300 import _native
+    M = arrow.ArrowMatrix(w.grid2d_64(), 64)
+    with pytest.raises(arrow.ArrowError) as e:
+        M.spmm(torch.zeros(4096, 12, device="cuda"), 1)       # 3 vectors of 16 B: not a power of two
+    assert e.value.code == _native.ARROW_EINVAL
+    M.spmm(torch.zeros(4096, 16, device="cuda", dtype=torch.bfloat16), 1)   # f32 values, bf16 X: allowed
+    Mb = arrow.ArrowMatrix(w.grid2d_64(), 64, value_dtype="bf16")
+    with pytest.raises(arrow.ArrowError) as e:
+        Mb.spmm(torch.zeros(4096, 16, device="cuda"), 1)      # bf16 values need 16-bit features
+    assert e.value.code == _native.ARROW_EINVAL
+    big = torch.zeros(4096 * 16 + 1, device="cuda")
+    L = _native.lib()
+    rc = L.arrow_spmm(M._h, _native.ctypes.c_void_p(big.data_ptr() + 4), 16, 1,
+                      _native.ctypes.c_void_p(big.data_ptr()), 0, 0, None)
+    assert rc == _native.ARROW_EINVAL                          # misaligned X
+
+
+def test_profile_events(arrow):
+    A = w.grid3d(20)
+    M = arrow.ArrowMatrix(A, 64)
+    Xd = torch.randn(A.n, 16, device="cuda")
+    M.spmm(Xd, 5, rescale=True, profile=True)
+    ms, cnt = M.profile_get(arrow.ARROW_K_ROWS)
+    assert cnt == 5 and ms > 0
+    assert M.profile_get(arrow.ARROW_K_NORM)[1] == 5
+    assert M.profile_get(arrow.ARROW_K_PERMUTE)[1] == 2
+    assert M.profile_get(arrow.ARROW_K_ROWS)[1] == 0           # read once, then forgotten
+
+
+# ---- full-size workloads (the launch configuration bench.py times) -----------------------
+
+def _sample_rows(n, count, seed):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.r_[0, n - 1, rng.integers(0, n, count)])
+
+
+def test_full_size_grid3d_400(arrow):
+    """3D 400^3 7-point grid (n = 64M, nnz = 447.04M), b = 4096, k = 16 f32, 20 iterations.
+
+    Sampled rows are computed by the oracle one by one (dependency cone of 20 hops);
+    with the rescale on, the column of ones must stay constant and every column has unit norm.
+    """
+    A = w.grid3d(400, seed=3)
+    assert A.n == 64_000_000 and A.nnz == 447_040_000
+    M = arrow.ArrowMatrix(A, 4096)
+    X = w.features(A.n, 16, seed=4)
+    X[:, 0] = 1.0
+    Xd = torch.from_numpy(X).cuda()
+    Y = M.spmm(Xd, 20)
+    rows = _sample_rows(A.n, 48, 1)
+    Ys = Y[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    R = S.iterate_rows(A, X, 20, rows)
+    assert np.max(np.abs(Ys - R)) <= 1e-5 * 20 * np.max(np.abs(R))
+    assert np.max(np.abs(Ys[:, 0] - 1.0)) <= 1e-5 * 20            # A row-normalised: A^t 1 = 1
+    Yr = M.spmm(Xd, 20, rescale=True)
+    nrm = torch.linalg.vector_norm(Yr.double(), dim=0).cpu().numpy()
+    assert np.allclose(nrm, 1.0, atol=1e-5)
+    c0 = Yr[:, 0].double()
+    assert float((c0 * np.sqrt(A.n) - 1.0).abs().max()) <= 1e-5 * 20
+    # the rescaled result is A^20 X times one factor per column: fit it, compare the rows
+    Yrs = Yr[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    c = np.sum(Yrs * R, axis=0) / np.sum(R * R, axis=0)
+    assert err_inf(Yrs, R * c) <= 1e-5 * 20

@@ -98,3 +98,13 @@ def test_decomposed_product_equals_plain_product():
         X = np.random.default_rng(1).standard_normal((A.n, 4))
         lv = D.la_decompose(A, b, seed=2)
         assert np.allclose(S.decomposed_product(lv, X), S.spmm(A, X), rtol=1e-13, atol=1e-13)
+
+
+def test_iterate_rows_equals_full_iteration():
+    for A, T in ((w.grid_stencil((9, 8, 7), seed=2), 4), (w.rmat_gcn(9, 8, seed=8), 3),
+                 (w.random_csr(200, 0.01, 3), 5)):
+        X = np.random.default_rng(T).standard_normal((A.n, 3))
+        rows = np.array([0, 5, A.n - 1, A.n // 2])
+        full = S.iterate(A, X, T)[rows]
+        assert np.allclose(S.iterate_rows(A, X, T, rows), full, rtol=1e-13, atol=1e-13)
+        assert np.allclose(S.iterate_rows(A, lambda r: X[r], T, rows), full, rtol=1e-13, atol=1e-13)
