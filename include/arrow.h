@@ -150,6 +150,7 @@ typedef struct {
     int32_t value_dtype;
     int64_t long_rows;       /* rows split into segments (head rows of hubs)        */
     int64_t segments;        /* segments of the split rows                           */
+    int64_t tiles;           /* row tiles of the fused row program                   */
     int64_t device_bytes;    /* bytes of device memory owned by the handle (no workspace) */
     double  decompose_seconds;
 } arrow_stats;
@@ -166,6 +167,18 @@ int arrow_get_stats(arrow_handle h, arrow_stats* s);
  * and number of launches.  Synchronises on the recorded events, then forgets them.
  * The events are measured on the stream the kernels were launched on. */
 int arrow_profile_get(arrow_handle h, int32_t kernel, double* total_ms, int64_t* launches);
+
+/* arrow_status -- synchronously read and clear the handle's device status word.  Kernels
+ * that wait on bulk copies give every wait a 2 s limit; when one runs out the kernel sets
+ * the word, waits (bounded) for its copies in flight and returns, so the context stays
+ * usable.  Returns ARROW_OK with *status = 0, or ARROW_ETIMEOUT with *status != 0. */
+int arrow_status(arrow_handle h, int32_t* status);
+
+/* arrow_selftest_timeout -- runs the bounded-wait path on purpose: a one-block kernel
+ * waits on an mbarrier that nothing completes, gives up after limit_ns (0 < limit <= 10 s)
+ * and sets its status word, which is copied to *status (1 = the wait ran out, as expected).
+ * Touches no handle; the context stays usable.  Errors: ARROW_EINVAL, ARROW_ECUDA. */
+int arrow_selftest_timeout(int64_t limit_ns, int32_t* status);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* arrow_last_error(void);

@@ -126,6 +126,12 @@ class ArrowMatrix:
                                                     vals.ctypes.data))
         return rowptr, colidx[:nz], vals[:nz]
 
+    def status(self) -> int:
+        """Read and clear the device status word (raises ArrowError on a timed-out wait)."""
+        st = ctypes.c_int32()
+        _native.check(_native.lib().arrow_status(self._h, ctypes.byref(st)))
+        return int(st.value)
+
     def stats(self) -> dict:
         s = _native.ArrowStats()
         _native.check(_native.lib().arrow_get_stats(self._h, ctypes.byref(s)))

@@ -43,7 +43,7 @@ class ArrowOpts(ctypes.Structure):
 class ArrowStats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("b", ctypes.c_int64),
                 ("levels", ctypes.c_int32), ("value_dtype", ctypes.c_int32),
-                ("long_rows", ctypes.c_int64), ("segments", ctypes.c_int64),
+                ("long_rows", ctypes.c_int64), ("segments", ctypes.c_int64), ("tiles", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("decompose_seconds", ctypes.c_double)]
 
 
@@ -67,6 +67,8 @@ SIGNATURES = {
     "arrow_level_csr": (_I32, [_P, _I32, _P, _P, _P]),
     "arrow_get_stats": (_I32, [_P, ctypes.POINTER(ArrowStats)]),
     "arrow_profile_get": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
+    "arrow_status": (_I32, [_P, ctypes.POINTER(_I32)]),
+    "arrow_selftest_timeout": (_I32, [_I64, ctypes.POINTER(_I32)]),
     "arrow_last_error": (ctypes.c_char_p, []),
 }
 

@@ -12,6 +12,13 @@ namespace arrow {
 
 void set_error(const std::string& msg);
 
+// Row tiles of the fused row program: at most kTileRows rows and kTileNnz entries each.
+// A tile's row pointers and entries are staged into shared memory with bulk copies.
+constexpr int kTileRows = 256;
+constexpr int kTileNnz = 2048;
+constexpr int kDefaultLongRow = 64;
+constexpr int kDefaultSegment = 512;
+
 // One level i of the decomposition A = sum_i P_{pi_i} B_i P_{pi_i}^T.
 struct Level {
     std::vector<int32_t> perm;   // vertex -> position (pi_i)
@@ -22,15 +29,20 @@ struct Level {
 // Device copy of the fused row program (see arrow_spmm.cu for how it is used).
 struct DeviceData {
     int device = -1;
-    int32_t* rowptr = nullptr;      // [n+1] into col/val, rows in pi_0 order
-    int32_t* col = nullptr;         // [nnz] pi_0 position of the X row each entry reads
-    void* val = nullptr;            // [nnz] values, value_dtype
+    int32_t* rowptr = nullptr;      // [n+1] short rows' entries (split rows are empty here)
+    int32_t* col = nullptr;         // [nnz_short] pi_0 position of the X row each entry reads
+    void* val = nullptr;            // [nnz_short] values, value_dtype
+    int32_t* tile_row = nullptr;    // [n_tiles+1] first row of each tile
+    int32_t* tile_ent = nullptr;    // [n_tiles+1] first entry of each tile
+    int32_t* lcol = nullptr;        // [nnz_long] entries of the split rows
+    void* lval = nullptr;           // [nnz_long]
     int32_t* perm0 = nullptr;       // [n]  vertex -> pi_0 position
     int32_t* iperm0 = nullptr;      // [n]  pi_0 position -> vertex
-    int32_t* long_rows = nullptr;   // [n_long] rows (pi_0 positions) split into segments, ascending
-    int32_t* long_segptr = nullptr; // [n_long+1] first segment of each long row
-    int32_t* seg_begin = nullptr;   // [n_seg] entry range of each segment
+    int32_t* long_rows = nullptr;   // [n_long] split rows (pi_0 positions), ascending
+    int32_t* long_segptr = nullptr; // [n_long+1] first segment of each split row
+    int32_t* seg_begin = nullptr;   // [n_seg] entry range of each segment in lcol/lval
     int32_t* seg_end = nullptr;     // [n_seg]
+    int32_t* status = nullptr;      // [1] device status word (0 = ok; set by bounded waits)
     size_t bytes = 0;
     // handle-owned workspace (arrow_spmm); arrow_spmm_ws uses the caller's instead
     void* ws = nullptr;
@@ -59,10 +71,13 @@ struct arrow_handle_s {
     std::vector<uint8_t> entry_level;   // level of every entry of A
     std::vector<arrow::Level> levels;
     // fused row program on the host (rows in pi_0 order), uploaded by arrow_upload
-    std::vector<int32_t> f_rowptr;      // [n+1]
-    std::vector<int32_t> f_col;         // [nnz] pi_0 position of the column vertex
-    std::vector<int32_t> f_src;         // [nnz] index of the entry in A (for its value)
+    std::vector<int32_t> f_rowptr;      // [n+1] short rows; split rows have no entries here
+    std::vector<int32_t> f_col;         // pi_0 position of the column vertex
+    std::vector<int32_t> f_src;         // index of the entry in A (for its value)
+    std::vector<int32_t> l_col, l_src;  // entries of the split rows
     std::vector<int32_t> long_rows, long_segptr, seg_begin, seg_end;
+    std::vector<int32_t> tile_row, tile_ent;
+    int32_t long_row = arrow::kDefaultLongRow;
     double decompose_seconds = 0.0;
     bool uploaded = false;
     arrow::DeviceData dev;

@@ -121,142 +121,244 @@ __device__ __forceinline__ float ld_stream_val<float>(const float* p) {
 }
 
 // ------------------------------------------------------------------------------------
+// bulk-copy (TMA) and mbarrier helpers
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared, completion counted on the mbarrier (addresses and size: multiples of 16 B)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of the given parity, giving up after limit_ns of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+
+// CTAs of the rows kernel resident per SM (register cap) and shared-memory carveout (%).
+#ifndef ARROW_ROWS_MIN_BLOCKS
+#define ARROW_ROWS_MIN_BLOCKS 3
+#endif
+#ifndef ARROW_ROWS_CARVEOUT
+#define ARROW_ROWS_CARVEOUT 50
+#endif
+constexpr int kStatusTimeout = 1;
+
+// ------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------
+// Shared-memory layout of one staged tile: row pointers, column indices, values, each a
+// 16-byte aligned superset of the tile's range.
+constexpr int kRpBytes = ((kTileRows + 1 + 6) * 4 + 15) / 16 * 16;
+constexpr int kColBytes = ((kTileNnz + 8) * 4 + 15) / 16 * 16;
+constexpr int kValBytes = kColBytes;
+constexpr int kBufBytes = (kRpBytes + kColBytes + kValBytes + 127) / 128 * 128;
+// + per-warp FP64 column sums of squares (8 warps x kc doubles) after the two buffers
+constexpr int kRowsSmemBase = 128 + 2 * kBufBytes;
+static inline int rows_smem_bytes(int kc) { return kRowsSmemBase + 8 * kc * 8; }
+
 struct RowArgs {
-    const int32_t* rowptr;
+    const int32_t* rowptr;     // short-row stream
     const int32_t* col;
     const void* val;
-    int64_t n;
-    const void* X;        // pi_0-ordered input, n x ldx
-    void* Y;              // pi_0-ordered output, n x ldx
-    int64_t ldx;          // k
-    int32_t koff;         // first column of this chunk
-    int32_t kc;           // columns of this chunk
-    int32_t long_row;     // rows with more entries are split
-    int32_t n_long;
-    const int32_t* long_rows;
-    const int32_t* long_segptr;
-    const float* partials;     // [n_seg][kc] segment partials of this chunk
+    const int32_t* tile_row;
+    const int32_t* tile_ent;
+    int32_t n_tiles;
+    const void* X;             // pi_0-ordered input, n x ldx
+    void* Y;                   // pi_0-ordered output, n x ldx
+    int64_t ldx;               // k
+    int32_t koff;              // first column of this chunk
+    int32_t kc;                // columns of this chunk
     const double* scale;       // [k] per-column factor d_{t-1}, or null
-    double* norm_partials;     // [gridDim.x][k], or null
+    double* norm_partials;     // [gridDim.x][k] (rows kernel slots), or null
+    int32_t* status;
 };
 
+// Thread 0: stage tile t (row pointers, columns, values) into buf with three bulk copies.
+template <typename TV>
+__device__ __forceinline__ void issue_tile(const RowArgs& a, int t, unsigned char* buf, uint64_t* bar) {
+    constexpr int VE = 16 / int(sizeof(TV));
+    const int r0 = a.tile_row[t], r1 = a.tile_row[t + 1];
+    const int e0 = a.tile_ent[t], e1 = a.tile_ent[t + 1];
+    const int ra = r0 & ~3, rb = (r1 + 1 + 3) & ~3;
+    const int ca = e0 & ~3, cb = (e1 + 3) & ~3;
+    const int va = e0 & ~(VE - 1), vb = (e1 + VE - 1) & ~(VE - 1);
+    const uint32_t brp = uint32_t(rb - ra) * 4u;
+    const uint32_t bcol = uint32_t(cb - ca) * 4u;
+    const uint32_t bval = uint32_t(vb - va) * uint32_t(sizeof(TV));
+    mbar_arrive_expect_tx(bar, brp + bcol + bval);
+    bulk_g2s(buf, a.rowptr + ra, brp, bar);
+    if (bcol) bulk_g2s(buf + kRpBytes, a.col + ca, bcol, bar);
+    if (bval) bulk_g2s(buf + kRpBytes + kColBytes, static_cast<const TV*>(a.val) + va, bval, bar);
+}
+
+// Fused arrow-row kernel (persistent).  Each CTA walks row tiles t = blockIdx.x, +gridDim.x,
+// ...; a tile's row pointers and entries arrive by bulk copy, two tiles in flight.  A team
+// of T lanes owns a row: it reads up to 8 entries from shared memory, issues their 16-byte
+// X gathers together, accumulates in FP32 in entry order (levels in order), scales,
+// stores the row and, with RESCALE, adds its squares to FP64 per-column partials.
 template <typename TX, typename TV, int T, bool RESCALE>
-__global__ void __launch_bounds__(256) arrow_rows_kernel(RowArgs a) {
+__global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(RowArgs a) {
     using P = Pack<TX>;
     constexpr int V = P::V;
+    constexpr int VE = 16 / int(sizeof(TV));
+    constexpr int TEAMS = 256 / T;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    unsigned char* bufs = smem + 128;
+    double* wsum = reinterpret_cast<double*>(smem + kRowsSmemBase);   // [8][kc]
     const int lane = threadIdx.x & 31;
-    const int tl = lane & (T - 1);
-    const int64_t team0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / T;
-    const int64_t nteams = (int64_t(gridDim.x) * blockDim.x) / T;
+    const int tl = threadIdx.x & (T - 1);
+    const int team = threadIdx.x / T;
     const int col0 = tl * V;
     const TX* __restrict__ X = static_cast<const TX*>(a.X) + a.koff + col0;
     TX* __restrict__ Y = static_cast<TX*>(a.Y) + a.koff + col0;
-    const TV* __restrict__ val = static_cast<const TV*>(a.val);
+    const int G = gridDim.x;
 
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    if (RESCALE)
+        for (int c = threadIdx.x; c < 8 * a.kc; c += blockDim.x) wsum[c] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (int(blockIdx.x) < a.n_tiles) issue_tile<TV>(a, blockIdx.x, bufs, &bar[0]);
+        if (int(blockIdx.x) + G < a.n_tiles) issue_tile<TV>(a, blockIdx.x + G, bufs + kBufBytes, &bar[1]);
+    }
     float scl[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) scl[v] = a.scale ? float(a.scale[a.koff + col0 + v]) : 1.0f;
     float sq[V];
-    double dsq[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) { sq[v] = 0.f; dsq[v] = 0.0; }
-    int nsq = 0;
+    for (int v = 0; v < V; ++v) sq[v] = 0.f;
 
-    for (int64_t r = team0; r < a.n; r += nteams) {
-        const int32_t s = __ldg(a.rowptr + r), e = __ldg(a.rowptr + r + 1);
-        float acc[V];
+    int i = 0;
+    int failed_at = -1;
+    for (int t = blockIdx.x; t < a.n_tiles; t += G, ++i) {
+        const int b = i & 1;
+        unsigned char* buf = bufs + b * kBufBytes;
+        const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) { failed_at = i; break; }
+        const int r0 = __ldg(a.tile_row + t), r1 = __ldg(a.tile_row + t + 1), e0 = __ldg(a.tile_ent + t);
+        const int32_t* srp = reinterpret_cast<const int32_t*>(buf) + (r0 & 3);
+        const int32_t* scol = reinterpret_cast<const int32_t*>(buf + kRpBytes) + (e0 & 3);
+        const TV* sval = reinterpret_cast<const TV*>(buf + kRpBytes + kColBytes) + (e0 & (VE - 1));
+        const int nrows = r1 - r0;
+        for (int j = team; j < nrows; j += TEAMS) {
+            const int s = srp[j] - e0, e = srp[j + 1] - e0;
+            float acc[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = 0.f;
-        if (e - s > a.long_row) {
-            int lo = 0, hi = a.n_long - 1;
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (__ldg(a.long_rows + mid) < r) lo = mid + 1; else hi = mid;
-            }
-            const int g0 = __ldg(a.long_segptr + lo), g1 = __ldg(a.long_segptr + lo + 1);
-            for (int g = g0; g < g1; ++g) {
-                const float4* p = reinterpret_cast<const float4*>(a.partials + int64_t(g) * a.kc + col0);
+            for (int v = 0; v < V; ++v) acc[v] = 0.f;
+            for (int base = s; base < e; base += 8) {
+                const int cnt = e - base;
+                uint4 x[8];
 #pragma unroll
-                for (int q = 0; q < V / 4; ++q) {
-                    float4 f = p[q];
-                    acc[4 * q + 0] += f.x; acc[4 * q + 1] += f.y; acc[4 * q + 2] += f.z; acc[4 * q + 3] += f.w;
+                for (int u = 0; u < 8; ++u)
+                    if (u < cnt) x[u] = ld_x(X + int64_t(scol[base + u]) * a.ldx);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (u < cnt) {
+                        const float w = val_to_float(sval[base + u]);
+                        float f[V];
+                        P::to_float(x[u], f);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = fmaf(w, f[v], acc[v]);
+                    }
                 }
             }
-        } else {
-            int32_t j = s;
-            for (; j + 4 <= e; j += 4) {
-                int32_t c[4];
-                float w[4];
-                uint4 x[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) c[u] = ld_stream_i32(a.col + j + u);
+            for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+            const uint4 out = P::from_float(acc);
+            *reinterpret_cast<uint4*>(Y + int64_t(r0 + j) * a.ldx) = out;
+            if (RESCALE) {
+                float yr[V];
+                P::to_float(out, yr);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) w[u] = val_to_float(ld_stream_val<TV>(val + j + u));
-#pragma unroll
-                for (int u = 0; u < 4; ++u) x[u] = ld_x(X + int64_t(c[u]) * a.ldx);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    float f[V];
-                    P::to_float(x[u], f);
-#pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] = fmaf(w[u], f[v], acc[v]);
-                }
-            }
-            for (; j < e; ++j) {
-                const int32_t c = ld_stream_i32(a.col + j);
-                const float w = val_to_float(ld_stream_val<TV>(val + j));
-                float f[V];
-                P::to_float(ld_x(X + int64_t(c) * a.ldx), f);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = fmaf(w, f[v], acc[v]);
+                for (int v = 0; v < V; ++v) sq[v] = fmaf(yr[v], yr[v], sq[v]);
             }
         }
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] *= scl[v];
-        const uint4 out = P::from_float(acc);
-        *reinterpret_cast<uint4*>(Y + r * a.ldx) = out;
         if (RESCALE) {
-            float yr[V];
-            P::to_float(out, yr);
+            // this tile's squares: teams of the warp (fixed xor butterfly, FP32), then the
+            // warp's FP64 running sum in shared memory
 #pragma unroll
-            for (int v = 0; v < V; ++v) sq[v] = fmaf(yr[v], yr[v], sq[v]);
-            if (++nsq == 8) {
+            for (int off = T; off < 32; off <<= 1)
 #pragma unroll
-                for (int v = 0; v < V; ++v) { dsq[v] += double(sq[v]); sq[v] = 0.f; }
-                nsq = 0;
-            }
+                for (int v = 0; v < V; ++v) sq[v] += __shfl_xor_sync(0xffffffffu, sq[v], off);
+            if (lane < T)
+#pragma unroll
+                for (int v = 0; v < V; ++v) wsum[(threadIdx.x >> 5) * a.kc + col0 + v] += double(sq[v]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) sq[v] = 0.f;
         }
+        __syncthreads();   // every thread is done with buf
+        if (threadIdx.x == 0 && t + 2 * G < a.n_tiles) issue_tile<TV>(a, t + 2 * G, buf, &bar[b]);
+    }
+    if (failed_at >= 0) {
+        // a staged tile never arrived: report, wait (bounded) for copies still in flight, leave
+        if (threadIdx.x == 0) {
+            atomicExch(a.status, kStatusTimeout);
+            const int t = blockIdx.x + failed_at * G;
+            mbar_wait_bounded(&bar[failed_at & 1], (failed_at >> 1) & 1, kWaitLimitNs);
+            if (t + G < a.n_tiles) mbar_wait_bounded(&bar[(failed_at + 1) & 1], ((failed_at + 1) >> 1) & 1, kWaitLimitNs);
+        }
+        return;
     }
     if (RESCALE) {
-        // FP64 column sums of squares: lanes -> warp (fixed butterfly) -> block (fixed order)
-#pragma unroll
-        for (int v = 0; v < V; ++v) dsq[v] += double(sq[v]);
-#pragma unroll
-        for (int off = T; off < 32; off <<= 1)
-#pragma unroll
-            for (int v = 0; v < V; ++v) dsq[v] += __shfl_xor_sync(0xffffffffu, dsq[v], off);
-        __shared__ double sh[8][256];
-        const int warp = threadIdx.x >> 5;
-        if (lane < T)
-#pragma unroll
-            for (int v = 0; v < V; ++v) sh[warp][col0 + v] = dsq[v];
+        // block's FP64 column sums: warps in fixed order
         __syncthreads();
-        const int nw = blockDim.x >> 5;
         for (int c = threadIdx.x; c < a.kc; c += blockDim.x) {
-            double t = 0.0;
-            for (int w = 0; w < nw; ++w) t += sh[w][c];
-            a.norm_partials[int64_t(blockIdx.x) * a.ldx + a.koff + c] = t;
+            double acc = 0.0;
+            for (int w = 0; w < 8; ++w) acc += wsum[w * a.kc + c];
+            a.norm_partials[int64_t(blockIdx.x) * a.ldx + a.koff + c] = acc;
         }
     }
+}
+
+// Self-test of the bounded wait: nothing ever arrives on this barrier, so the wait must
+// give up after limit_ns and report through the status word.
+__global__ void arrow_selftest_wait_kernel(int32_t* status, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(status, kStatusTimeout);
 }
 
 struct SegArgs {
     const int32_t* seg_begin;
     const int32_t* seg_end;
     int64_t n_seg;
-    const int32_t* col;
+    const int32_t* col;        // split-row stream
     const void* val;
     const void* X;
     int64_t ldx;
@@ -319,6 +421,79 @@ __global__ void __launch_bounds__(256) arrow_segments_kernel(SegArgs a) {
             float4* p = reinterpret_cast<float4*>(a.partials + g * a.kc + col0);
 #pragma unroll
             for (int q = 0; q < V / 4; ++q) p[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+    }
+}
+
+struct CombArgs {
+    const int32_t* long_rows;
+    const int32_t* long_segptr;
+    int32_t n_long;
+    const float* partials;     // [n_seg][kc]
+    void* Y;
+    int64_t ldx;
+    int32_t koff, kc;
+    const double* scale;
+    double* norm_partials;     // [gridDim.x][k] (combine slots), or null
+};
+
+// Second stage of the head-row reduction: a team per split row adds its segment partials
+// in segment order, scales and stores the row (overwriting the zero the rows kernel wrote).
+template <typename TX, int T, bool RESCALE>
+__global__ void __launch_bounds__(256) arrow_combine_kernel(CombArgs a) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    const int lane = threadIdx.x & 31;
+    const int tl = threadIdx.x & (T - 1);
+    const int col0 = tl * V;
+    const int64_t team0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / T;
+    const int64_t nteams = (int64_t(gridDim.x) * blockDim.x) / T;
+    TX* __restrict__ Y = static_cast<TX*>(a.Y) + a.koff + col0;
+    float scl[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) scl[v] = a.scale ? float(a.scale[a.koff + col0 + v]) : 1.0f;
+    double dsq[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) dsq[v] = 0.0;
+    for (int64_t li = team0; li < a.n_long; li += nteams) {
+        float acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.f;
+        const int g0 = __ldg(a.long_segptr + li), g1 = __ldg(a.long_segptr + li + 1);
+        for (int g = g0; g < g1; ++g) {
+            const float4* p = reinterpret_cast<const float4*>(a.partials + int64_t(g) * a.kc + col0);
+#pragma unroll
+            for (int q = 0; q < V / 4; ++q) {
+                const float4 f = p[q];
+                acc[4 * q + 0] += f.x; acc[4 * q + 1] += f.y; acc[4 * q + 2] += f.z; acc[4 * q + 3] += f.w;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+        const uint4 out = P::from_float(acc);
+        *reinterpret_cast<uint4*>(Y + int64_t(__ldg(a.long_rows + li)) * a.ldx) = out;
+        if (RESCALE) {
+            float yr[V];
+            P::to_float(out, yr);
+#pragma unroll
+            for (int v = 0; v < V; ++v) dsq[v] += double(yr[v]) * double(yr[v]);
+        }
+    }
+    if (RESCALE) {
+#pragma unroll
+        for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+            for (int v = 0; v < V; ++v) dsq[v] += __shfl_xor_sync(0xffffffffu, dsq[v], off);
+        __shared__ double sh[8][256];
+        const int warp = threadIdx.x >> 5;
+        if (lane < T)
+#pragma unroll
+            for (int v = 0; v < V; ++v) sh[warp][col0 + v] = dsq[v];
+        __syncthreads();
+        for (int c = threadIdx.x; c < a.kc; c += blockDim.x) {
+            double acc = 0.0;
+            for (int w = 0; w < 8; ++w) acc += sh[w][c];
+            a.norm_partials[int64_t(blockIdx.x) * a.ldx + a.koff + c] = acc;
         }
     }
 }
@@ -400,7 +575,8 @@ static int cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 static void free_device(DeviceData& d) {
-    void* ptrs[] = {d.rowptr, d.col, d.val, d.perm0, d.iperm0, d.long_rows, d.long_segptr, d.seg_begin, d.seg_end, d.ws};
+    void* ptrs[] = {d.rowptr, d.col, d.val, d.tile_row, d.tile_ent, d.lcol, d.lval, d.perm0, d.iperm0,
+                    d.long_rows, d.long_segptr, d.seg_begin, d.seg_end, d.status, d.ws};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     int dev = d.device;
@@ -446,13 +622,49 @@ static void destroy_events(arrow_handle_s* h) {
     h->event_pool.clear();
 }
 
+// Device copies are padded by 64 bytes so that 16-byte rounded bulk copies of a range's
+// tail stay inside the allocation.
+constexpr size_t kPad = 64;
+
 template <typename T>
 static int upload_vec(T** dst, const std::vector<T>& src, size_t& bytes) {
     *dst = nullptr;
     if (src.empty()) return ARROW_OK;
-    ACK(cudaMalloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T)));
-    bytes += src.size() * sizeof(T);
+    ACK(cudaMalloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T) + kPad));
+    bytes += src.size() * sizeof(T) + kPad;
     ACK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    ACK(cudaMemset(reinterpret_cast<char*>(*dst) + src.size() * sizeof(T), 0, kPad));
+    return ARROW_OK;
+}
+
+// values of A gathered through src (index into A's entries), converted on the device
+static int upload_values(const arrow_handle_s* h, const std::vector<int32_t>& src, void** dst, size_t& bytes) {
+    *dst = nullptr;
+    const int64_t m = int64_t(src.size());
+    if (m == 0) return ARROW_OK;
+    const size_t sv = h->opts.value_dtype == ARROW_F32 ? 4 : 2;
+    std::vector<double> vals(m);
+    for (int64_t j = 0; j < m; ++j) vals[j] = h->values[src[j]];
+    double* tmp = nullptr;
+    ACK(cudaMalloc(&tmp, m * sizeof(double)));
+    cudaError_t e = cudaMemcpy(tmp, vals.data(), m * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(dst, m * sv + kPad);
+    if (e == cudaSuccess) {
+        bytes += m * sv + kPad;
+        e = cudaMemset(static_cast<char*>(*dst) + m * sv, 0, kPad);
+    }
+    if (e == cudaSuccess) {
+        const int grid = int(std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, int64_t(h->dev.sm_count) * 16)));
+        switch (h->opts.value_dtype) {
+            case ARROW_F32: arrow_convert_values_kernel<float><<<grid, 256>>>(tmp, static_cast<float*>(*dst), m); break;
+            case ARROW_BF16: arrow_convert_values_kernel<__nv_bfloat16><<<grid, 256>>>(tmp, static_cast<__nv_bfloat16*>(*dst), m); break;
+            default: arrow_convert_values_kernel<__half><<<grid, 256>>>(tmp, static_cast<__half*>(*dst), m); break;
+        }
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "arrow_upload: values");
     return ARROW_OK;
 }
 
@@ -464,10 +676,14 @@ static int upload_impl(arrow_handle_s* h) {
     int rc;
     if ((rc = upload_vec(&d.rowptr, h->f_rowptr, d.bytes))) return rc;
     if ((rc = upload_vec(&d.col, h->f_col, d.bytes))) return rc;
+    if ((rc = upload_vec(&d.tile_row, h->tile_row, d.bytes))) return rc;
+    if ((rc = upload_vec(&d.tile_ent, h->tile_ent, d.bytes))) return rc;
+    if ((rc = upload_vec(&d.lcol, h->l_col, d.bytes))) return rc;
     if ((rc = upload_vec(&d.long_rows, h->long_rows, d.bytes))) return rc;
     if ((rc = upload_vec(&d.long_segptr, h->long_segptr, d.bytes))) return rc;
     if ((rc = upload_vec(&d.seg_begin, h->seg_begin, d.bytes))) return rc;
     if ((rc = upload_vec(&d.seg_end, h->seg_end, d.bytes))) return rc;
+    if ((rc = upload_vec(&d.status, std::vector<int32_t>(4, 0), d.bytes))) return rc;
     const int64_t n = h->n;
     {
         std::vector<int32_t> perm0(n), iperm0(n);
@@ -480,37 +696,36 @@ static int upload_impl(arrow_handle_s* h) {
         if ((rc = upload_vec(&d.perm0, perm0, d.bytes))) return rc;
         if ((rc = upload_vec(&d.iperm0, iperm0, d.bytes))) return rc;
     }
-    const int64_t nnz = h->nnz;
-    if (nnz > 0) {
-        std::vector<double> vals(nnz);
-        for (int64_t j = 0; j < nnz; ++j) vals[j] = h->values[h->f_src[j]];
-        double* tmp = nullptr;
-        ACK(cudaMalloc(&tmp, nnz * sizeof(double)));
-        cudaError_t e = cudaMemcpy(tmp, vals.data(), nnz * sizeof(double), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc(&d.val, nnz * dtype_size(h->opts.value_dtype));
-        if (e == cudaSuccess) {
-            d.bytes += nnz * dtype_size(h->opts.value_dtype);
-            const int grid = std::max(1, std::min<int>(int((nnz + 255) / 256), d.sm_count * 16));
-            switch (h->opts.value_dtype) {
-                case ARROW_F32: arrow_convert_values_kernel<float><<<grid, 256>>>(tmp, static_cast<float*>(d.val), nnz); break;
-                case ARROW_BF16: arrow_convert_values_kernel<__nv_bfloat16><<<grid, 256>>>(tmp, static_cast<__nv_bfloat16*>(d.val), nnz); break;
-                default: arrow_convert_values_kernel<__half><<<grid, 256>>>(tmp, static_cast<__half*>(d.val), nnz); break;
-            }
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        }
-        cudaFree(tmp);
-        if (e != cudaSuccess) return cuda_fail(e, "arrow_upload: values");
-    }
+    if ((rc = upload_values(h, h->f_src, &d.val, d.bytes))) return rc;
+    if ((rc = upload_values(h, h->l_src, &d.lval, d.bytes))) return rc;
     return ARROW_OK;
 }
 
 // ---- launch plumbing -----------------------------------------------------------------
 struct Plan {
     int V, T, chunks, kc;
-    int rows_grid;   // CTAs of the row kernel (= number of FP64 norm partials)
+    int rows_grid;   // CTAs of the rows kernel (= its FP64 norm partial slots)
+    int comb_grid;   // CTAs of the combine kernel (= its partial slots after the rows kernel's)
     size_t x_bytes, part_bytes, np_bytes, sc_bytes, total;
 };
+
+template <typename TX, typename TV, int T, bool R>
+static int rows_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        constexpr int kc = T * Pack<TX>::V;
+        cudaFuncSetAttribute(arrow_rows_kernel<TX, TV, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             rows_smem_bytes(kc));
+        cudaFuncSetAttribute(arrow_rows_kernel<TX, TV, T, R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             ARROW_ROWS_CARVEOUT);
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, arrow_rows_kernel<TX, TV, T, R>, 256,
+                                                          rows_smem_bytes(kc)) != cudaSuccess || nb < 1)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
 
 static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags, Plan& p) {
     p.V = int(16 / dtype_size(x_dtype));
@@ -524,14 +739,17 @@ static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags,
         p.T = 32; p.chunks = int(t / 32);
     }
     p.kc = p.T * p.V;
-    const int64_t teams_per_block = 256 / p.T;
-    const int64_t need = (h->n + teams_per_block - 1) / teams_per_block;
     const int sm = h->dev.sm_count > 0 ? h->dev.sm_count : 1;
-    p.rows_grid = int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(sm) * 8)));
+    // persistent rows kernel: up to 4 CTAs per SM (the occupancy bound is applied at launch)
+    const int64_t n_tiles = h->tile_row.empty() ? 0 : int64_t(h->tile_row.size()) - 1;
+    p.rows_grid = int(std::max<int64_t>(1, std::min<int64_t>(n_tiles, int64_t(sm) * ARROW_ROWS_MIN_BLOCKS)));
+    const int64_t n_long = int64_t(h->long_rows.size());
+    const int64_t teams = 256 / p.T;
+    p.comb_grid = n_long ? int(std::max<int64_t>(1, std::min<int64_t>((n_long + teams - 1) / teams, int64_t(sm) * 2))) : 0;
     const size_t sx = dtype_size(x_dtype);
     p.x_bytes = align256(size_t(h->n) * size_t(k) * sx);
     p.part_bytes = align256(std::max<size_t>(1, h->seg_begin.size()) * size_t(p.kc) * 4);
-    p.np_bytes = (flags & ARROW_RESCALE) ? align256(size_t(p.rows_grid) * size_t(k) * 8) : 0;
+    p.np_bytes = (flags & ARROW_RESCALE) ? align256(size_t(p.rows_grid + p.comb_grid) * size_t(k) * 8) : 0;
     p.sc_bytes = (flags & ARROW_RESCALE) ? align256(2 * size_t(k) * 8) : 0;
     p.total = 2 * p.x_bytes + p.part_bytes + p.np_bytes + p.sc_bytes;
     return ARROW_OK;
@@ -541,25 +759,39 @@ template <typename TX, typename TV, int T>
 static void launch_step(const arrow_handle_s* h, const Plan& p, const TX* cur, TX* nxt, int64_t k, float* part,
                         const double* scale_in, double* np, cudaStream_t s, Prof& pf) {
     const DeviceData& d = h->dev;
+    const int32_t n_tiles = h->tile_row.empty() ? 0 : int32_t(h->tile_row.size()) - 1;
     for (int ch = 0; ch < p.chunks; ++ch) {
         const int koff = ch * p.kc;
         if (!h->seg_begin.empty()) {
-            SegArgs sa{d.seg_begin, d.seg_end, int64_t(h->seg_begin.size()), d.col, d.val, cur, k, koff, p.kc, part};
+            SegArgs sa{d.seg_begin, d.seg_end, int64_t(h->seg_begin.size()), d.lcol, d.lval, cur, k, koff, p.kc, part};
             const int64_t warps = int64_t(h->seg_begin.size());
             const int grid = int(std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, int64_t(d.sm_count) * 8)));
             cudaEvent_t e0 = pf.begin();
             arrow_segments_kernel<TX, TV, T><<<grid, 256, 0, s>>>(sa);
             pf.end(ARROW_K_SEGMENTS, e0);
         }
-        const int32_t long_row = h->opts.long_row > 0 ? h->opts.long_row : 64;
-        RowArgs ra{d.rowptr, d.col, d.val, h->n, cur, nxt, k, koff, p.kc, long_row, int32_t(h->long_rows.size()),
-                   d.long_rows, d.long_segptr, part, scale_in, np};
+        RowArgs ra{d.rowptr, d.col, d.val, d.tile_row, d.tile_ent, n_tiles, cur, nxt, k, koff, p.kc, scale_in, np, d.status};
         cudaEvent_t e0 = pf.begin();
-        if (np)
-            arrow_rows_kernel<TX, TV, T, true><<<p.rows_grid, 256, 0, s>>>(ra);
-        else
-            arrow_rows_kernel<TX, TV, T, false><<<p.rows_grid, 256, 0, s>>>(ra);
+        if (np) {
+            const int grid = std::min(p.rows_grid, d.sm_count * rows_blocks_per_sm<TX, TV, T, true>());
+            // the norm partial slots are indexed by blockIdx.x: unused slots must hold zero
+            if (grid < p.rows_grid) cudaMemsetAsync(np, 0, size_t(p.rows_grid) * size_t(k) * 8, s);
+            arrow_rows_kernel<TX, TV, T, true><<<grid, 256, rows_smem_bytes(p.kc), s>>>(ra);
+        } else {
+            const int grid = std::min(p.rows_grid, d.sm_count * rows_blocks_per_sm<TX, TV, T, false>());
+            arrow_rows_kernel<TX, TV, T, false><<<grid, 256, rows_smem_bytes(p.kc), s>>>(ra);
+        }
         pf.end(ARROW_K_ROWS, e0);
+        if (p.comb_grid) {
+            CombArgs ca{d.long_rows, d.long_segptr, int32_t(h->long_rows.size()), part, nxt, k, koff, p.kc, scale_in,
+                        np ? np + size_t(p.rows_grid) * size_t(k) : nullptr};
+            cudaEvent_t e1 = pf.begin();
+            if (np)
+                arrow_combine_kernel<TX, T, true><<<p.comb_grid, 256, 0, s>>>(ca);
+            else
+                arrow_combine_kernel<TX, T, false><<<p.comb_grid, 256, 0, s>>>(ca);
+            pf.end(ARROW_K_SEGMENTS, e1);
+        }
     }
 }
 
@@ -582,7 +814,7 @@ static void run_steps(const arrow_handle_s* h, const Plan& p, TX* xa, TX* xb, in
         }
         if (rescale) {
             cudaEvent_t e0 = pf.begin();
-            arrow_norm_finalize_kernel<<<int(k), 256, 0, s>>>(np, p.rows_grid, k, sc + (t & 1) * k);
+            arrow_norm_finalize_kernel<<<int(k), 256, 0, s>>>(np, p.rows_grid + p.comb_grid, k, sc + (t & 1) * k);
             pf.end(ARROW_K_NORM, e0);
         }
         std::swap(cur, nxt);
@@ -850,6 +1082,40 @@ int arrow_profile_get(arrow_handle h, int32_t kernel, double* total_ms, int64_t*
     return ARROW_OK;
 }
 
+int arrow_status(arrow_handle h, int32_t* status) {
+    if (!h || !status) { set_error("arrow_status: NULL argument"); return ARROW_EINVAL; }
+    if (!h->uploaded) { set_error("arrow_status: handle is not uploaded"); return ARROW_ESTATE; }
+    int32_t v = 0;
+    ACK(cudaMemcpy(&v, h->dev.status, sizeof(v), cudaMemcpyDeviceToHost));
+    *status = v;
+    if (v) {
+        const int32_t zero = 0;
+        ACK(cudaMemcpy(h->dev.status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+        set_error("arrow_status: a bounded device-side wait ran out");
+        return ARROW_ETIMEOUT;
+    }
+    return ARROW_OK;
+}
+
+int arrow_selftest_timeout(int64_t limit_ns, int32_t* status) {
+    if (!status || limit_ns <= 0 || limit_ns > 10000000000ll) {
+        set_error("arrow_selftest_timeout: status NULL or limit outside (0, 10 s]");
+        return ARROW_EINVAL;
+    }
+    int32_t* d = nullptr;
+    ACK(cudaMalloc(&d, sizeof(int32_t)));
+    cudaError_t e = cudaMemset(d, 0, sizeof(int32_t));
+    if (e == cudaSuccess) {
+        arrow_selftest_wait_kernel<<<1, 64>>>(d, uint64_t(limit_ns));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(status, d, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "arrow_selftest_timeout");
+    return ARROW_OK;
+}
+
 int arrow_get_stats(arrow_handle h, arrow_stats* s) {
     if (!h || !s) { set_error("arrow_get_stats: NULL argument"); return ARROW_EINVAL; }
     s->n = h->n;
@@ -858,6 +1124,7 @@ int arrow_get_stats(arrow_handle h, arrow_stats* s) {
     s->levels = int32_t(h->levels.size());
     s->value_dtype = h->opts.value_dtype;
     s->long_rows = int64_t(h->long_rows.size());
+    s->tiles = h->tile_row.empty() ? 0 : int64_t(h->tile_row.size()) - 1;
     s->segments = int64_t(h->seg_begin.size());
     s->device_bytes = int64_t(h->dev.bytes);
     s->decompose_seconds = h->decompose_seconds;

@@ -544,18 +544,43 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
     // Fused row program: row p of pi_0 holds the entries of vertex v = pi_0^{-1}(p) of
     // every level, in level order, inside a level in increasing level position of the
     // column (the CSR order of B_i).  Each entry reads X row pi_0(column vertex).
+    // Rows with more than long_row entries (the head rows of hubs) are split: their
+    // entries move to a separate stream cut into fixed-size segments, and their range
+    // in the short-row stream is empty.
     if (!band) {
         std::vector<int32_t> iperm0(n);
         const int32_t* perm0 = nl ? h->levels[0].perm.data() : nullptr;
         if (nl) for (int64_t v = 0; v < n; ++v) iperm0[perm0[v]] = int32_t(v);
         else std::iota(iperm0.begin(), iperm0.end(), 0);
+        const int32_t long_row = std::min(o.long_row > 0 ? o.long_row : kDefaultLongRow, kTileNnz);
+        const int32_t seg = o.segment > 0 ? o.segment : kDefaultSegment;
+        h->long_row = long_row;
+        std::vector<int32_t> len(n);
+        for (int64_t p = 0; p < n; ++p) len[p] = int32_t(A->rowptr[iperm0[p] + 1] - A->rowptr[iperm0[p]]);
         h->f_rowptr.assign(n + 1, 0);
+        h->long_rows.clear(); h->long_segptr.assign(1, 0); h->seg_begin.clear(); h->seg_end.clear();
+        std::vector<int64_t> lptr;   // start of each split row in the long stream
+        int64_t nl_ent = 0;
         for (int64_t p = 0; p < n; ++p) {
-            int32_t v = iperm0[p];
-            h->f_rowptr[p + 1] = h->f_rowptr[p] + int32_t(A->rowptr[v + 1] - A->rowptr[v]);
+            const bool is_long = len[p] > long_row;
+            h->f_rowptr[p + 1] = h->f_rowptr[p] + (is_long ? 0 : len[p]);
+            if (is_long) {
+                h->long_rows.push_back(int32_t(p));
+                lptr.push_back(nl_ent);
+                for (int32_t j = 0; j < len[p]; j += seg) {
+                    h->seg_begin.push_back(int32_t(nl_ent + j));
+                    h->seg_end.push_back(int32_t(nl_ent + std::min(len[p], j + seg)));
+                }
+                h->long_segptr.push_back(int32_t(h->seg_begin.size()));
+                nl_ent += len[p];
+            }
         }
-        h->f_col.resize(nnz);
-        h->f_src.resize(nnz);
+        h->f_col.resize(h->f_rowptr[n]);
+        h->f_src.resize(h->f_rowptr[n]);
+        h->l_col.resize(nl_ent);
+        h->l_src.resize(nl_ent);
+        std::vector<int32_t> long_index(n, -1);
+        for (size_t i = 0; i < h->long_rows.size(); ++i) long_index[h->long_rows[i]] = int32_t(i);
         pfor(n, [&](int64_t bb, int64_t e, int) {
             std::vector<std::pair<uint64_t, int32_t>> tmp;
             for (int64_t p = bb; p < e; ++p) {
@@ -567,26 +592,36 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
                     tmp.push_back({key, int32_t(j)});
                 }
                 std::sort(tmp.begin(), tmp.end());
-                int64_t o = h->f_rowptr[p];
-                for (auto& x : tmp) {
-                    h->f_col[o] = perm0[A->colidx[x.second]];
-                    h->f_src[o] = x.second;
-                    ++o;
+                int32_t* dcol;
+                int32_t* dsrc;
+                if (long_index[p] >= 0) {
+                    dcol = h->l_col.data() + lptr[long_index[p]];
+                    dsrc = h->l_src.data() + lptr[long_index[p]];
+                } else {
+                    dcol = h->f_col.data() + h->f_rowptr[p];
+                    dsrc = h->f_src.data() + h->f_rowptr[p];
+                }
+                for (size_t q = 0; q < tmp.size(); ++q) {
+                    dcol[q] = perm0[A->colidx[tmp[q].second]];
+                    dsrc[q] = tmp[q].second;
                 }
             }
         });
-        const int32_t long_row = o.long_row > 0 ? o.long_row : 64;
-        const int32_t seg = o.segment > 0 ? o.segment : 512;
-        h->long_rows.clear(); h->long_segptr.assign(1, 0); h->seg_begin.clear(); h->seg_end.clear();
-        for (int64_t p = 0; p < n; ++p) {
-            int32_t s = h->f_rowptr[p], e = h->f_rowptr[p + 1];
-            if (e - s <= long_row) continue;
-            h->long_rows.push_back(int32_t(p));
-            for (int32_t j = s; j < e; j += seg) {
-                h->seg_begin.push_back(j);
-                h->seg_end.push_back(std::min(e, j + seg));
+        // row tiles: consecutive rows, at most kTileRows rows and kTileNnz entries
+        h->tile_row.assign(1, 0);
+        h->tile_ent.assign(1, 0);
+        int64_t r = 0;
+        while (r < n) {
+            int64_t r1 = r, ent = 0;
+            while (r1 < n && r1 - r < kTileRows) {
+                int64_t l = h->f_rowptr[r1 + 1] - h->f_rowptr[r1];
+                if (ent + l > kTileNnz) break;
+                ent += l;
+                ++r1;
             }
-            h->long_segptr.push_back(int32_t(h->seg_begin.size()));
+            h->tile_row.push_back(int32_t(r1));
+            h->tile_ent.push_back(h->f_rowptr[r1]);
+            r = r1;
         }
     }
     h->decompose_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -151,3 +151,4 @@ def test_fused_program_stats(arrow):
     deg = np.diff(A.rowptr)
     assert s["long_rows"] == int((deg > 32).sum())
     assert s["segments"] == int(np.sum((deg[deg > 32] + 63) // 64))
+    assert s["tiles"] >= (A.n + 255) // 256

@@ -179,6 +179,22 @@ def test_profile_events(arrow):
     assert M.profile_get(arrow.ARROW_K_ROWS)[1] == 0           # read once, then forgotten
 
 
+def test_status_word_and_bounded_wait_selftest(arrow):
+    import ctypes
+    import time
+    from paper_2402_19364_gb300 import _native
+    A = w.grid3d(16)
+    M = arrow.ArrowMatrix(A, 64)
+    M.spmm(torch.randn(A.n, 16, device="cuda"), 3)
+    assert M.status() == 0                                     # no wait ran out
+    st = ctypes.c_int32(-1)
+    t0 = time.time()
+    _native.check(_native.lib().arrow_selftest_timeout(50_000_000, ctypes.byref(st)))
+    assert st.value == 1 and time.time() - t0 < 5.0            # gave up after ~50 ms, reported it
+    Y = M.spmm(torch.ones(A.n, 16, device="cuda"), 2)          # context still usable
+    assert torch.allclose(Y, torch.ones_like(Y), atol=1e-5)
+
+
 # ---- full-size workloads (the launch configuration bench.py times) -----------------------
 
 def _sample_rows(n, count, seed):
