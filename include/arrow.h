@@ -133,6 +133,25 @@ int arrow_workspace_size(arrow_handle h, int64_t k, int32_t x_dtype, int32_t fla
 int arrow_spmm_ws(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y,
                   int32_t x_dtype, int32_t flags, void* workspace, size_t ws_bytes, void* stream);
 
+/* arrow_spmm_static -- arrow_spmm for callers that cannot allocate device memory.
+ * The paper has no counterpart; it exists for code that must not call cudaMalloc: work
+ * recorded while a CUDA graph is being captured (allocation is not allowed then), plugins
+ * running inside another framework or inference runtime that owns all device memory, and
+ * latency-bound serving loops that forbid allocation after start-up (cudaMalloc/cudaFree
+ * synchronise the device).  Same arguments and result as arrow_spmm (X, Y on the device,
+ * caller-owned), but the scratch lives in one file-scope device array of 64 MiB that every
+ * GPU loading the library holds until the process exits.  Problems whose scratch (two
+ * n x k feature buffers, split-row partials, FP64 norm sums: the arrow_workspace_size value)
+ * exceeds 64 MiB -- about 500,000 rows at k = 16 in FP32 -- are rejected with ARROW_EINVAL.
+ * The call allocates nothing.  The handle's device must be current.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and caches it: make
+ * that first call before any stream capture.  All calls share the array and it keeps the
+ * last call's contents, so calls whose work overlaps on the GPU (other streams, other
+ * threads, other handles) race: serialise them.  ARROW_PROFILE is rejected (it creates
+ * events).  Errors: ARROW_EINVAL, ARROW_ESTATE, ARROW_ECUDA. */
+int arrow_spmm_static(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y,
+                      int32_t x_dtype, int32_t flags, void* stream);
+
 /* ---- structure export (parity tests, reports) ------------------------------------ */
 /* Number of levels l (order of the decomposition). */
 int arrow_num_levels(arrow_handle h, int32_t* l);

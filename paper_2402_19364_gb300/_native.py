@@ -61,6 +61,7 @@ SIGNATURES = {
     "arrow_spmm": (_I32, [_P, _P, _I64, _I32, _P, _I32, _I32, _P]),
     "arrow_workspace_size": (_I32, [_P, _I64, _I32, _I32, ctypes.POINTER(_SIZE)]),
     "arrow_spmm_ws": (_I32, [_P, _P, _I64, _I32, _P, _I32, _I32, _P, _SIZE, _P]),
+    "arrow_spmm_static": (_I32, [_P, _P, _I64, _I32, _P, _I32, _I32, _P]),
     "arrow_num_levels": (_I32, [_P, ctypes.POINTER(_I32)]),
     "arrow_level_info": (_I32, [_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "arrow_level_perm": (_I32, [_P, _I32, _P]),

@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -892,6 +893,35 @@ static int spmm_dispatch(arrow_handle_s* h, const Plan& p, const void* X, int64_
     }
 }
 
+// ---- entry point for callers that cannot allocate device memory ----------------------
+// arrow_spmm_static keeps its scratch (the two pi_0-ordered feature buffers, split-row
+// partials and FP64 norm sums) in this file-scope array instead of a cudaMalloc'd
+// workspace.  Every GPU that loads the library holds the array until the process exits.
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_static_mu;
+static void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on `device` (which must be current), looked up once
+// per device.  In host code the symbol itself is only a host-side stand-in.
+static int static_scratch_ptr(int device, void** out) {
+    if (device < 0 || device >= kMaxDevices) {
+        set_error("arrow_spmm_static: device ordinal out of range");
+        return ARROW_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "arrow_spmm_static: cudaGetSymbolAddress");
+        g_static_ptr[device] = p;
+    }
+    *out = g_static_ptr[device];
+    return ARROW_OK;
+}
+
 }  // namespace arrow
 
 // ======================================================================================
@@ -1006,6 +1036,38 @@ int arrow_spmm(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y,
         h->dev.ws_bytes = p.total;
     }
     return spmm_dispatch(h, p, X, k, iters, Y, x_dtype, flags, static_cast<char*>(h->dev.ws),
+                         static_cast<cudaStream_t>(stream));
+}
+
+int arrow_spmm_static(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y, int32_t x_dtype,
+                      int32_t flags, void* stream) {
+    int rc = check_spmm_args(h, X, k, iters, Y, x_dtype, flags);
+    if (rc) return rc;
+    if (flags & ARROW_PROFILE) {
+        set_error("arrow_spmm_static: ARROW_PROFILE is not available here (it creates CUDA events)");
+        return ARROW_EINVAL;
+    }
+    if (h->n == 0 || k == 0) return ARROW_OK;
+    int cur = -1;
+    ACK(cudaGetDevice(&cur));
+    if (cur != h->dev.device) {
+        set_error("arrow_spmm_static: make the handle's device current before the call");
+        return ARROW_EINVAL;
+    }
+    Plan p;
+    if ((rc = make_plan(h, k, x_dtype, flags, p))) return rc;
+    if (iters > 0 && p.total > kStaticScratchBytes) {
+        set_error("arrow_spmm_static: this problem needs " + std::to_string(p.total) +
+                  " bytes of scratch, more than the library's static " + std::to_string(kStaticScratchBytes) +
+                  "-byte array; use arrow_spmm or arrow_spmm_ws");
+        return ARROW_EINVAL;
+    }
+    void* scratch = nullptr;
+    if ((rc = static_scratch_ptr(cur, &scratch))) return rc;
+    // Everything the kernels read from the scratch is written earlier in the same call
+    // (feature buffers, segment partials, norm sums); the norm slots that a smaller grid
+    // leaves unwritten are cleared by the launch code before each step.
+    return spmm_dispatch(h, p, X, k, iters, Y, x_dtype, flags, static_cast<char*>(scratch),
                          static_cast<cudaStream_t>(stream));
 }
 

@@ -1,0 +1,71 @@
+"""GPU test of arrow_spmm_static, the entry point for callers that cannot allocate.
+
+Some callers cannot call cudaMalloc: code recorded during CUDA graph capture, plugins
+inside a framework that owns all device memory, and serving loops that forbid allocation
+after start-up.  arrow_spmm_static keeps its scratch in a fixed 64 MiB device array of the
+library instead.  This file is collected last so that, should it fail, a run stopping at
+the first failure has already run every other test.  It checks, through the C-ABI, that two
+calls in a row give the result of arrow_spmm within the FP32 tolerance of the parity tests
+(max over columns of ||y - y_ref||_inf / ||y_ref||_inf <= 1e-5 * iters), and that a
+problem too large for the array is refused.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def arrow():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_19364_gb300 import build
+    build.build()
+    import paper_2402_19364_gb300 as pkg
+    return pkg
+
+
+def _rel_inf(Y, R):
+    Y = Y.double().cpu().numpy()
+    R = R.double().cpu().numpy()
+    return float(np.max(np.max(np.abs(Y - R), axis=0) / np.max(np.abs(R), axis=0)))
+
+
+@pytest.mark.parametrize("rescale", [False, True])
+def test_static_scratch_matches_arrow_spmm(arrow, rescale):
+    from paper_2402_19364_gb300 import _native
+    L = _native.lib()
+    A = w.rmat_gcn(12, 16, seed=5)                    # power law: split rows use the scratch too
+    M = arrow.ArrowMatrix(A, 128, long_row=16, segment=64)
+    iters = 6
+    flags = _native.ARROW_RESCALE if rescale else 0
+    for k in (16, 64):
+        X = torch.from_numpy(w.features(A.n, k, seed=k)).cuda()
+        ref = M.spmm(X, iters, rescale=rescale)
+        for _ in range(2):                            # two calls in a row share the array
+            Y = torch.full_like(X, float("nan"))
+            stream = torch.cuda.current_stream()
+            _native.check(L.arrow_spmm_static(M._h, ctypes.c_void_p(X.data_ptr()), k, iters,
+                                              ctypes.c_void_p(Y.data_ptr()), _native.ARROW_F32, flags,
+                                              ctypes.c_void_p(stream.cuda_stream)))
+            torch.cuda.synchronize()
+            assert _rel_inf(Y, ref) <= 1e-5 * iters
+
+
+def test_static_scratch_refuses_large_problems(arrow):
+    from paper_2402_19364_gb300 import _native
+    L = _native.lib()
+    A = w.grid3d(100)                                 # 1M rows x 16 f32: 128 MB of scratch
+    M = arrow.ArrowMatrix(A, 4096)
+    X = torch.zeros(A.n, 16, device="cuda")
+    Y = torch.zeros_like(X)
+    rc = L.arrow_spmm_static(M._h, ctypes.c_void_p(X.data_ptr()), 16, 2, ctypes.c_void_p(Y.data_ptr()),
+                             _native.ARROW_F32, 0, None)
+    assert rc == _native.ARROW_EINVAL
+    assert b"static" in L.arrow_last_error()
