@@ -95,6 +95,11 @@ int arrow_decompose(const arrow_csr* A, int64_t b, const arrow_opts* o, arrow_ha
  * No-op if already uploaded.  Errors: ARROW_EINVAL (band predicate), ARROW_ENOMEM, ARROW_ECUDA. */
 int arrow_upload(arrow_handle h);
 
+/* arrow_handle_copy -- a second handle with the same decomposition (no re-decomposition),
+ * storing A's values in value_dtype; uploaded if h is.  *out is NULL on failure.
+ * Errors: ARROW_EINVAL, ARROW_ENOMEM, ARROW_ECUDA. */
+int arrow_handle_copy(arrow_handle h, int32_t value_dtype, arrow_handle* out);
+
 /* Release the handle and all host and device memory it owns.  NULL-safe.
  * Must not be called while work that uses the handle is still running on a stream. */
 void arrow_free(arrow_handle h);
@@ -151,6 +156,35 @@ int arrow_spmm_ws(arrow_handle h, const void* X, int64_t k, int32_t iters, void*
  * events).  Errors: ARROW_EINVAL, ARROW_ESTATE, ARROW_ECUDA. */
 int arrow_spmm_static(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y,
                       int32_t x_dtype, int32_t flags, void* stream);
+
+/* ---- batches: many matrices advanced together --------------------------------------- */
+#define ARROW_GRAPH 0x4   /* arrow_batch_spmm flags: capture the call once as a CUDA graph, replay it */
+
+typedef struct arrow_batch_s* arrow_batch;   /* opaque, library-owned */
+
+/* arrow_batch_create -- group count uploaded handles (same device, same value dtype) so that
+ * one call advances all of them.  The handles must outlive the batch.  Not in the paper (its
+ * matrices are advanced by separate rank groups, Alg. 2); this is the one-GPU batching of many
+ * independent problems.  Errors: ARROW_EINVAL, ARROW_ESTATE (a handle not uploaded), ARROW_ECUDA. */
+int arrow_batch_create(const arrow_handle* handles, int32_t count, arrow_batch* out);
+
+/* arrow_batch_spmm -- for every matrix m: Y[m] = A_m^iters X[m] (sigma = identity), with
+ * X[m], Y[m] DEVICE pointers (host arrays of count pointers), row-major n_m x k[m], 16-byte
+ * aligned, element type x_dtype; k[m] = V * 2^j with V = 16 / sizeof(x_dtype) and k[m] / V <= 32.
+ * Each iteration of the whole batch is one launch per kernel class (split-row segments,
+ * rows, split-row combine) over the work units of all matrices; the permutes are one launch
+ * each.  Results are bit-identical to arrow_spmm on each matrix alone.  flags: 0 or
+ * ARROW_GRAPH (capture once, replay while X, Y, k, iters and dtype stay the same).  The call
+ * allocates its workspace on first use or growth (outside any capture) and synchronises
+ * the stream when X, Y, k or dtype change.  Errors: ARROW_EINVAL, ARROW_ECUDA. */
+int arrow_batch_spmm(arrow_batch b, const void* const* X, void* const* Y, const int64_t* k, int32_t iters,
+                     int32_t x_dtype, int32_t flags, void* stream);
+
+/* Read and clear the batch's device status word (see arrow_status). */
+int arrow_batch_status(arrow_batch b, int32_t* status);
+
+/* Release the batch (not its handles).  NULL-safe. */
+void arrow_batch_free(arrow_batch b);
 
 /* ---- structure export (parity tests, reports) ------------------------------------ */
 /* Number of levels l (order of the decomposition). */

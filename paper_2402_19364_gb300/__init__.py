@@ -12,11 +12,11 @@ import ctypes
 import numpy as np
 
 from . import _native
-from ._native import (ARROW_BF16, ARROW_F16, ARROW_F32, ARROW_HOST_ONLY, ARROW_K_NORM, ARROW_K_PERMUTE,
+from ._native import (ARROW_BF16, ARROW_F16, ARROW_F32, ARROW_GRAPH, ARROW_HOST_ONLY, ARROW_K_NORM, ARROW_K_PERMUTE,
                       ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_PRED_BAND, ARROW_PRED_BLOCK, ARROW_PROFILE,
                       ARROW_RESCALE, ArrowError)
 
-__all__ = ["ArrowMatrix", "ArrowError", "dtype_code", "ARROW_F32", "ARROW_BF16", "ARROW_F16"]
+__all__ = ["ArrowMatrix", "ArrowBatch", "ArrowError", "dtype_code", "ARROW_F32", "ARROW_BF16", "ARROW_F16"]
 
 _DTYPE_NAMES = {"f32": ARROW_F32, "float32": ARROW_F32, "bf16": ARROW_BF16, "bfloat16": ARROW_BF16,
                 "f16": ARROW_F16, "float16": ARROW_F16}
@@ -96,6 +96,14 @@ class ArrowMatrix:
 
     def __exit__(self, *exc):
         self.close()
+
+    def copy(self, value_dtype) -> "ArrowMatrix":
+        """``arrow_handle_copy``: same decomposition, values stored in ``value_dtype``."""
+        out = ArrowMatrix.__new__(ArrowMatrix)
+        out._h = ctypes.c_void_p()
+        _native.check(_native.lib().arrow_handle_copy(self._h, dtype_code(value_dtype), ctypes.byref(out._h)))
+        out.n, out.nnz, out.b, out.value_dtype = self.n, self.nnz, self.b, dtype_code(value_dtype)
+        return out
 
     def upload(self) -> None:
         _native.check(_native.lib().arrow_upload(self._h))
@@ -193,3 +201,51 @@ class ArrowMatrix:
         x_bytes = total_active * k * sx
         y_bytes = self.n * k * sx
         return {"A": a_bytes, "X": x_bytes, "Y": y_bytes, "total": a_bytes + x_bytes + y_bytes}
+
+
+class ArrowBatch:
+    """``arrow_batch_create`` over uploaded :class:`ArrowMatrix` handles (kept alive here)."""
+
+    def __init__(self, mats):
+        self.mats = list(mats)
+        arr = (ctypes.c_void_p * len(self.mats))(*[m._h.value for m in self.mats])
+        self._b = ctypes.c_void_p()
+        _native.check(_native.lib().arrow_batch_create(arr, len(self.mats), ctypes.byref(self._b)))
+
+    def spmm(self, Xs, iters: int, *, outs=None, graph: bool = False, stream=None):
+        """Ys[m] = A_m^iters Xs[m] for every matrix in one ``arrow_batch_spmm`` call."""
+        import torch
+        if len(Xs) != len(self.mats):
+            raise ValueError("one X per matrix")
+        if outs is None:
+            outs = [torch.empty_like(x) for x in Xs]
+        xd = {dtype_code(x.dtype) for x in Xs}
+        if len(xd) != 1:
+            raise ValueError("all X must share one dtype")
+        for m, x, y in zip(self.mats, Xs, outs):
+            if not (x.is_cuda and x.is_contiguous() and x.dim() == 2 and x.shape[0] == m.n and y.shape == x.shape
+                    and y.dtype == x.dtype and y.is_contiguous()):
+                raise ValueError("X[m], Y[m] must be contiguous CUDA (n_m, k_m) tensors of one dtype")
+        n = len(Xs)
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Xs])
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in outs])
+        ks = (ctypes.c_int64 * n)(*[x.shape[1] for x in Xs])
+        _native.check(_native.lib().arrow_batch_spmm(self._b, xp, yp, ks, int(iters), xd.pop(),
+                                                     ARROW_GRAPH if graph else 0, _stream_ptr(stream)))
+        return outs
+
+    def status(self) -> int:
+        st = ctypes.c_int32()
+        _native.check(_native.lib().arrow_batch_status(self._b, ctypes.byref(st)))
+        return int(st.value)
+
+    def close(self) -> None:
+        if getattr(self, "_b", None) and self._b.value:
+            _native.lib().arrow_batch_free(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

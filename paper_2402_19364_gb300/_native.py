@@ -20,6 +20,7 @@ ARROW_PRED_BLOCK, ARROW_PRED_BAND = 0, 1
 ARROW_HOST_ONLY = 0x1
 ARROW_RESCALE = 0x1
 ARROW_PROFILE = 0x2
+ARROW_GRAPH = 0x4
 ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_K_NORM, ARROW_K_PERMUTE = 0, 1, 2, 3
 
 
@@ -58,6 +59,11 @@ SIGNATURES = {
     "arrow_decompose": (_I32, [ctypes.POINTER(ArrowCsr), _I64, ctypes.POINTER(ArrowOpts), ctypes.POINTER(_P)]),
     "arrow_upload": (_I32, [_P]),
     "arrow_free": (None, [_P]),
+    "arrow_handle_copy": (_I32, [_P, _I32, ctypes.POINTER(_P)]),
+    "arrow_batch_create": (_I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)]),
+    "arrow_batch_spmm": (_I32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64), _I32, _I32, _I32, _P]),
+    "arrow_batch_status": (_I32, [_P, ctypes.POINTER(_I32)]),
+    "arrow_batch_free": (None, [_P]),
     "arrow_spmm": (_I32, [_P, _P, _I64, _I32, _P, _I32, _I32, _P]),
     "arrow_workspace_size": (_I32, [_P, _I64, _I32, _I32, ctypes.POINTER(_SIZE)]),
     "arrow_spmm_ws": (_I32, [_P, _P, _I64, _I32, _P, _I32, _I32, _P, _SIZE, _P]),

@@ -32,134 +32,12 @@
 #include <vector>
 
 #include "arrow_internal.h"
+#include "device_common.cuh"
 
 namespace arrow {
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
-
-// ------------------------------------------------------------------------------------
-// element packing: one 16-byte vector of X holds V elements
-// ------------------------------------------------------------------------------------
-template <typename TX>
-struct Pack;
-
-template <>
-struct Pack<float> {
-    static constexpr int V = 4;
-    __device__ __forceinline__ static void to_float(const uint4& u, float* f) {
-        f[0] = __uint_as_float(u.x); f[1] = __uint_as_float(u.y);
-        f[2] = __uint_as_float(u.z); f[3] = __uint_as_float(u.w);
-    }
-    __device__ __forceinline__ static uint4 from_float(const float* f) {
-        return make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]), __float_as_uint(f[3]));
-    }
-};
-
-__device__ __forceinline__ void bf16x2_to_float(uint32_t w, float& lo, float& hi) {
-    lo = __uint_as_float(w << 16);
-    hi = __uint_as_float(w & 0xffff0000u);
-}
-
-template <>
-struct Pack<__nv_bfloat16> {
-    static constexpr int V = 8;
-    __device__ __forceinline__ static void to_float(const uint4& u, float* f) {
-        bf16x2_to_float(u.x, f[0], f[1]); bf16x2_to_float(u.y, f[2], f[3]);
-        bf16x2_to_float(u.z, f[4], f[5]); bf16x2_to_float(u.w, f[6], f[7]);
-    }
-    __device__ __forceinline__ static uint32_t pack2(float a, float b) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<uint32_t*>(&h);
-    }
-    __device__ __forceinline__ static uint4 from_float(const float* f) {
-        return make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
-    }
-};
-
-template <>
-struct Pack<__half> {
-    static constexpr int V = 8;
-    __device__ __forceinline__ static void h2(uint32_t w, float& lo, float& hi) {
-        __half2 h = *reinterpret_cast<__half2*>(&w);
-        float2 f = __half22float2(h);
-        lo = f.x; hi = f.y;
-    }
-    __device__ __forceinline__ static void to_float(const uint4& u, float* f) {
-        h2(u.x, f[0], f[1]); h2(u.y, f[2], f[3]); h2(u.z, f[4], f[5]); h2(u.w, f[6], f[7]);
-    }
-    __device__ __forceinline__ static uint32_t pack2(float a, float b) {
-        __half2 h = __floats2half2_rn(a, b);
-        return *reinterpret_cast<uint32_t*>(&h);
-    }
-    __device__ __forceinline__ static uint4 from_float(const float* f) {
-        return make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
-    }
-};
-
-__device__ __forceinline__ float val_to_float(float v) { return v; }
-__device__ __forceinline__ float val_to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
-__device__ __forceinline__ float val_to_float(__half v) { return __half2float(v); }
-
-__device__ __forceinline__ uint4 ld_x(const void* p) {
-    uint4 r;
-    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
-    return r;
-}
-__device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
-    int32_t r;
-    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(r) : "l"(p));
-    return r;
-}
-template <typename TV>
-__device__ __forceinline__ TV ld_stream_val(const TV* p) { return __ldg(p); }
-template <>
-__device__ __forceinline__ float ld_stream_val<float>(const float* p) {
-    float r;
-    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(r) : "l"(p));
-    return r;
-}
-
-// ------------------------------------------------------------------------------------
-// bulk-copy (TMA) and mbarrier helpers
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// 1-D bulk copy global -> shared, completion counted on the mbarrier (addresses and size: multiples of 16 B)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait for the phase of the given parity, giving up after limit_ns of wall time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-}
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
 
 // CTAs of the rows kernel resident per SM (register cap) and shared-memory carveout (%).
 #ifndef ARROW_ROWS_MIN_BLOCKS
@@ -168,17 +46,10 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
 #ifndef ARROW_ROWS_CARVEOUT
 #define ARROW_ROWS_CARVEOUT 50
 #endif
-constexpr int kStatusTimeout = 1;
 
 // ------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------
-// Shared-memory layout of one staged tile: row pointers, column indices, values, each a
-// 16-byte aligned superset of the tile's range.
-constexpr int kRpBytes = ((kTileRows + 1 + 6) * 4 + 15) / 16 * 16;
-constexpr int kColBytes = ((kTileNnz + 8) * 4 + 15) / 16 * 16;
-constexpr int kValBytes = kColBytes;
-constexpr int kBufBytes = (kRpBytes + kColBytes + kValBytes + 127) / 128 * 128;
 // + per-warp FP64 column sums of squares (8 warps x kc doubles) after the two buffers
 constexpr int kRowsSmemBase = 128 + 2 * kBufBytes;
 static inline int rows_smem_bytes(int kc) { return kRowsSmemBase + 8 * kc * 8; }
@@ -203,19 +74,8 @@ struct RowArgs {
 // Thread 0: stage tile t (row pointers, columns, values) into buf with three bulk copies.
 template <typename TV>
 __device__ __forceinline__ void issue_tile(const RowArgs& a, int t, unsigned char* buf, uint64_t* bar) {
-    constexpr int VE = 16 / int(sizeof(TV));
-    const int r0 = a.tile_row[t], r1 = a.tile_row[t + 1];
-    const int e0 = a.tile_ent[t], e1 = a.tile_ent[t + 1];
-    const int ra = r0 & ~3, rb = (r1 + 1 + 3) & ~3;
-    const int ca = e0 & ~3, cb = (e1 + 3) & ~3;
-    const int va = e0 & ~(VE - 1), vb = (e1 + VE - 1) & ~(VE - 1);
-    const uint32_t brp = uint32_t(rb - ra) * 4u;
-    const uint32_t bcol = uint32_t(cb - ca) * 4u;
-    const uint32_t bval = uint32_t(vb - va) * uint32_t(sizeof(TV));
-    mbar_arrive_expect_tx(bar, brp + bcol + bval);
-    bulk_g2s(buf, a.rowptr + ra, brp, bar);
-    if (bcol) bulk_g2s(buf + kRpBytes, a.col + ca, bcol, bar);
-    if (bval) bulk_g2s(buf + kRpBytes + kColBytes, static_cast<const TV*>(a.val) + va, bval, bar);
+    stage_tile<TV>(a.rowptr, a.col, static_cast<const TV*>(a.val), a.tile_row[t], a.tile_row[t + 1], a.tile_ent[t],
+                   a.tile_ent[t + 1], buf, bar);
 }
 
 // Fused arrow-row kernel (persistent).  Each CTA walks row tiles t = blockIdx.x, +gridDim.x,
@@ -515,27 +375,60 @@ __global__ void __launch_bounds__(256) arrow_norm_finalize_kernel(const double* 
     if (threadIdx.x == 0) scale_out[c] = sh[0] > 0.0 ? 1.0 / sqrt(sh[0]) : 1.0;
 }
 
-// dst[r] = src[idx[r]] (* scale per column), 16-byte vectors.
+// dst[r] = src[idx[r]] (* scale per column), 16-byte vectors.  nv = k / V vectors per row is
+// a power of two <= 32 (a warp covers 32 / nv rows per pass) or a multiple of 32 (a warp per
+// row); every thread keeps U row gathers in flight.
 template <typename TX>
 __global__ void __launch_bounds__(256) arrow_gather_rows_kernel(const TX* __restrict__ src, TX* __restrict__ dst,
                                                                 const int32_t* __restrict__ idx, int64_t n, int64_t k,
                                                                 const double* __restrict__ scale) {
     using P = Pack<TX>;
     constexpr int V = P::V;
-    const int64_t nv = k / V;
-    const int64_t total = n * nv;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t r = i / nv, q = i - r * nv;
-        const int64_t s = __ldg(idx + r);
-        uint4 u = ld_x(src + s * k + q * V);
-        if (scale) {
-            float f[V];
-            P::to_float(u, f);
+    constexpr int U = 4;
+    const int nv = int(k / V);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    if (nv <= 32) {
+        const int rpw = 32 / nv, lr = lane / nv, lq = lane - lr * nv;
+        for (int64_t g = warp; g * rpw < n; g += nwarps * U) {
+            uint4 u[U];
 #pragma unroll
-            for (int v = 0; v < V; ++v) f[v] = float(double(f[v]) * scale[q * V + v]);
-            u = P::from_float(f);
+            for (int j = 0; j < U; ++j) {
+                const int64_t r = (g + j * nwarps) * rpw + lr;
+                if (r < n) u[j] = ld_x(src + int64_t(__ldg(idx + r)) * k + lq * V);
+            }
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int64_t r = (g + j * nwarps) * rpw + lr;
+                if (r < n) {
+                    uint4 o = u[j];
+                    if (scale) {
+                        float f[V];
+                        P::to_float(o, f);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) f[v] = float(double(f[v]) * scale[lq * V + v]);
+                        o = P::from_float(f);
+                    }
+                    *reinterpret_cast<uint4*>(dst + r * k + lq * V) = o;
+                }
+            }
         }
-        *reinterpret_cast<uint4*>(dst + r * k + q * V) = u;
+    } else {
+        for (int64_t r = warp; r < n; r += nwarps) {
+            const int64_t s = __ldg(idx + r);
+            for (int q = lane; q < nv; q += 32) {
+                uint4 o = ld_x(src + s * k + q * V);
+                if (scale) {
+                    float f[V];
+                    P::to_float(o, f);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) f[v] = float(double(f[v]) * scale[q * V + v]);
+                    o = P::from_float(f);
+                }
+                *reinterpret_cast<uint4*>(dst + r * k + q * V) = o;
+            }
+        }
     }
 }
 
@@ -565,7 +458,7 @@ static size_t dtype_size(int dt) { return dt == ARROW_F32 ? 4 : 2; }
 static bool dtype_ok(int dt) { return dt >= ARROW_F32 && dt <= ARROW_F16; }
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-static int cuda_fail(cudaError_t e, const char* what) {
+int cuda_fail(cudaError_t e, const char* what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? ARROW_ENOMEM : ARROW_ECUDA;
 }
@@ -834,7 +727,7 @@ static int spmm_typed(const arrow_handle_s* h, const Plan& p, const void* X, int
     double* sc = reinterpret_cast<double*>(ws + 2 * p.x_bytes + p.part_bytes + p.np_bytes);
     const int64_t n = h->n;
     const int64_t vecs = n * (k / p.V);
-    const int ggrid = int(std::max<int64_t>(1, std::min<int64_t>((vecs + 255) / 256, int64_t(d.sm_count) * 16)));
+    const int ggrid = int(std::max<int64_t>(1, std::min<int64_t>((vecs + 1023) / 1024, int64_t(d.sm_count) * 8)));
     cudaEvent_t e0 = pf.begin();
     arrow_gather_rows_kernel<TX><<<ggrid, 256, 0, s>>>(static_cast<const TX*>(X), xa, d.iperm0, n, k, nullptr);
     pf.end(ARROW_K_PERMUTE, e0);
@@ -981,6 +874,37 @@ int arrow_upload(arrow_handle h) {
     }
     if (rc != ARROW_OK) { free_device(h->dev); return rc; }
     h->uploaded = true;
+    return ARROW_OK;
+}
+
+int arrow_handle_copy(arrow_handle h, int32_t value_dtype, arrow_handle* out) {
+    if (!out) { set_error("arrow_handle_copy: out is NULL"); return ARROW_EINVAL; }
+    *out = nullptr;
+    if (!h || value_dtype < ARROW_F32 || value_dtype > ARROW_F16) {
+        set_error("arrow_handle_copy: bad handle or value dtype");
+        return ARROW_EINVAL;
+    }
+    arrow_handle_s* c = nullptr;
+    try {
+        c = new arrow_handle_s();
+        c->n = h->n; c->nnz = h->nnz; c->b = h->b; c->opts = h->opts;
+        c->opts.value_dtype = value_dtype;
+        c->rowptr = h->rowptr; c->colidx = h->colidx; c->values = h->values; c->entry_level = h->entry_level;
+        c->levels = h->levels;
+        c->f_rowptr = h->f_rowptr; c->f_col = h->f_col; c->f_src = h->f_src; c->l_col = h->l_col; c->l_src = h->l_src;
+        c->long_rows = h->long_rows; c->long_segptr = h->long_segptr; c->seg_begin = h->seg_begin; c->seg_end = h->seg_end;
+        c->tile_row = h->tile_row; c->tile_ent = h->tile_ent; c->long_row = h->long_row;
+        c->decompose_seconds = h->decompose_seconds;
+    } catch (const std::bad_alloc&) {
+        delete c;
+        set_error("arrow_handle_copy: host allocation failed");
+        return ARROW_ENOMEM;
+    }
+    if (h->uploaded) {
+        int rc = arrow_upload(c);
+        if (rc != ARROW_OK) { arrow_free(c); return rc; }
+    }
+    *out = c;
     return ARROW_OK;
 }
 

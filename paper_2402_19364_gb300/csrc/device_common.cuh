@@ -1,0 +1,165 @@
+// Device helpers shared by the single-matrix (arrow_spmm.cu) and batched (arrow_batch.cu)
+// kernels: 16-byte element packing, streaming loads, mbarrier / bulk-copy (TMA) primitives
+// with bounded waits, and the shared-memory layout of a staged row tile.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "arrow_internal.h"
+
+namespace arrow {
+
+// ------------------------------------------------------------------------------------
+// element packing: one 16-byte vector of X holds V elements
+// ------------------------------------------------------------------------------------
+template <typename TX>
+struct Pack;
+
+template <>
+struct Pack<float> {
+    static constexpr int V = 4;
+    __device__ __forceinline__ static void to_float(const uint4& u, float* f) {
+        f[0] = __uint_as_float(u.x); f[1] = __uint_as_float(u.y);
+        f[2] = __uint_as_float(u.z); f[3] = __uint_as_float(u.w);
+    }
+    __device__ __forceinline__ static uint4 from_float(const float* f) {
+        return make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]), __float_as_uint(f[3]));
+    }
+};
+
+__device__ __forceinline__ void bf16x2_to_float(uint32_t w, float& lo, float& hi) {
+    lo = __uint_as_float(w << 16);
+    hi = __uint_as_float(w & 0xffff0000u);
+}
+
+template <>
+struct Pack<__nv_bfloat16> {
+    static constexpr int V = 8;
+    __device__ __forceinline__ static void to_float(const uint4& u, float* f) {
+        bf16x2_to_float(u.x, f[0], f[1]); bf16x2_to_float(u.y, f[2], f[3]);
+        bf16x2_to_float(u.z, f[4], f[5]); bf16x2_to_float(u.w, f[6], f[7]);
+    }
+    __device__ __forceinline__ static uint32_t pack2(float a, float b) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+    __device__ __forceinline__ static uint4 from_float(const float* f) {
+        return make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+    }
+};
+
+template <>
+struct Pack<__half> {
+    static constexpr int V = 8;
+    __device__ __forceinline__ static void h2(uint32_t w, float& lo, float& hi) {
+        __half2 h = *reinterpret_cast<__half2*>(&w);
+        float2 f = __half22float2(h);
+        lo = f.x; hi = f.y;
+    }
+    __device__ __forceinline__ static void to_float(const uint4& u, float* f) {
+        h2(u.x, f[0], f[1]); h2(u.y, f[2], f[3]); h2(u.z, f[4], f[5]); h2(u.w, f[6], f[7]);
+    }
+    __device__ __forceinline__ static uint32_t pack2(float a, float b) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+    __device__ __forceinline__ static uint4 from_float(const float* f) {
+        return make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+    }
+};
+
+__device__ __forceinline__ float val_to_float(float v) { return v; }
+__device__ __forceinline__ float val_to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float val_to_float(__half v) { return __half2float(v); }
+
+__device__ __forceinline__ uint4 ld_x(const void* p) {
+    uint4 r;
+    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
+    int32_t r;
+    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+template <typename TV>
+__device__ __forceinline__ TV ld_stream_val(const TV* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float ld_stream_val<float>(const float* p) {
+    float r;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(r) : "l"(p));
+    return r;
+}
+
+// ------------------------------------------------------------------------------------
+// bulk-copy (TMA) and mbarrier helpers
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared, completion counted on the mbarrier (addresses and size: multiples of 16 B)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of the given parity, giving up after limit_ns of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+constexpr int kStatusTimeout = 1;
+
+// Shared-memory layout of one staged tile: row pointers, column indices, values, each a
+// 16-byte aligned superset of the tile's range.
+constexpr int kRpBytes = ((kTileRows + 1 + 6) * 4 + 15) / 16 * 16;
+constexpr int kColBytes = ((kTileNnz + 8) * 4 + 15) / 16 * 16;
+constexpr int kValBytes = kColBytes;
+constexpr int kBufBytes = (kRpBytes + kColBytes + kValBytes + 127) / 128 * 128;
+
+// Stage the row tile [r0, r1) with entries [e0, e1) into buf: row pointers, columns and values,
+// each as a 16-byte aligned superset (the arrays are padded by 64 bytes), completing on bar.
+template <typename TV>
+__device__ __forceinline__ void stage_tile(const int32_t* rowptr, const int32_t* col, const TV* val, int r0, int r1,
+                                           int e0, int e1, unsigned char* buf, uint64_t* bar) {
+    constexpr int VE = 16 / int(sizeof(TV));
+    const int ra = r0 & ~3, rb = (r1 + 1 + 3) & ~3;
+    const int ca = e0 & ~3, cb = (e1 + 3) & ~3;
+    const int va = e0 & ~(VE - 1), vb = (e1 + VE - 1) & ~(VE - 1);
+    const uint32_t brp = uint32_t(rb - ra) * 4u;
+    const uint32_t bcol = uint32_t(cb - ca) * 4u;
+    const uint32_t bval = uint32_t(vb - va) * uint32_t(sizeof(TV));
+    mbar_arrive_expect_tx(bar, brp + bcol + bval);
+    bulk_g2s(buf, rowptr + ra, brp, bar);
+    if (bcol) bulk_g2s(buf + kRpBytes, col + ca, bcol, bar);
+    if (bval) bulk_g2s(buf + kRpBytes + kColBytes, val + va, bval, bar);
+}
+
+}  // namespace arrow
