@@ -41,7 +41,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="grid3d", choices=["grid3d", "grid2d", "rmat"])
+    p.add_argument("--workload", default="grid3d", choices=["grid3d", "grid2d", "rmat", "batch"])
+    p.add_argument("--count", type=int, default=0, help="matrices of the batch workload (0 = 512)")
     p.add_argument("--size", type=int, default=0, help="grid side / R-MAT scale (0 = workload default)")
     p.add_argument("--iters", type=int, default=0)
     p.add_argument("--k", type=int, default=0)
@@ -227,8 +228,109 @@ def run_reference(a, spec):
     print(json.dumps(line), flush=True)
 
 
+def _batch_worker(task):
+    """Spawned worker: generate one random-geometric matrix, decompose it on the host, save it."""
+    i, n, seed, path, vdt = task
+    import workloads as w
+    import paper_2402_19364_gb300 as arrow
+    A = w.rgg(int(n), seed=seed)
+    b = int(math.ceil(math.sqrt(A.n)))
+    M = arrow.ArrowMatrix(A, b, host_only=True, nthreads=1, value_dtype=vdt)
+    M.save(path)
+    return i, A.n, A.nnz, b
+
+
+def run_batch(a):
+    """Batched workload: `count` random-geometric graphs (n log-uniform in [1e3, 2e6], b = ceil(sqrt n),
+    k in {8,16,32,64}, FP16 values and features, 10 iterations each) advanced by arrow_batch_spmm as one
+    CUDA graph, against the FP32 form with one arrow_spmm call (one rows launch per iteration) per matrix."""
+    import multiprocessing as mp
+    import tempfile
+    import torch
+    import workloads as w
+    from paper_2402_19364_gb300 import build as _build
+    _build.build()
+    import paper_2402_19364_gb300 as arrow
+    count = a.count or 512
+    iters = a.iters or 10
+    sizes = w.log_uniform_sizes(count, 1e3, 2e6, 7)
+    ks = [int(x) for x in np.random.default_rng(8).choice([8, 16, 32, 64], count)]
+    tmp = tempfile.mkdtemp(prefix="arrow_batch_", dir="/dev/shm" if os.path.isdir("/dev/shm") else None)
+    tasks = sorted([(i, int(sizes[i]), 7000 + i, os.path.join(tmp, f"m{i}.arw"), "f16") for i in range(count)],
+                   key=lambda t: -t[1])
+    t0 = time.perf_counter()
+    info = {}
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        for i, n, nnz, b in pool.imap_unordered(_batch_worker, tasks):
+            info[i] = (n, nnz, b)
+    t_prep = time.perf_counter() - t0
+    torch.cuda.set_device(0)
+    mats16, mats32 = [], []
+    for i in range(count):
+        path = os.path.join(tmp, f"m{i}.arw")
+        m16 = arrow.ArrowMatrix.load(path)
+        mats16.append(m16)
+        mats32.append(m16.copy("f32"))
+        os.remove(path)
+    os.rmdir(tmp)
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    X16 = [torch.randn(m.n, k, device="cuda", generator=gen).half() for m, k in zip(mats16, ks)]
+    Y16 = [torch.empty_like(x) for x in X16]
+    X32 = [x.float() for x in X16]
+    Y32 = [torch.empty_like(x) for x in X32]
+    B = arrow.ArrowBatch(mats16)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(max(3, a.warmup)):
+        B.spmm(X16, iters, outs=Y16, graph=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(a.steps):
+        B.spmm(X16, iters, outs=Y16, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / a.steps
+    assert B.status() == 0
+    for m, x, y in zip(mats32, X32, Y32):
+        m.spmm(x, iters, out=y)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(a.steps):
+        for m, x, y in zip(mats32, X32, Y32):
+            m.spmm(x, iters, out=y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_f = e0.elapsed_time(e1) / a.steps
+    err = 0.0
+    for y16, y32 in zip(Y16, Y32):
+        err = max(err, float((torch.linalg.vector_norm(y16.float() - y32, dim=0) /
+                              torch.linalg.vector_norm(y32, dim=0)).max()))
+    bytes16 = sum(m.algorithmic_bytes_per_iter(k, "f16")["total"] for m, k in zip(mats16, ks)) * iters
+    bytes32 = sum(m.algorithmic_bytes_per_iter(k, "f32")["total"] for m, k in zip(mats32, ks)) * iters
+    rows = sum(m.n for m in mats16)
+    nnz = sum(m.nnz for m in mats16)
+    peak, peak_kind = load_peaks()
+    out = {"metric": "arrow-SpMM batched matrix-iterations/s (512 random-geometric graphs, one CUDA graph)",
+           "value": count * iters / (ms_b / 1e3), "unit": "matrix-iters/s", "n_gpus": 1, "steps": a.steps,
+           "warmup": max(3, a.warmup), "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+           "config": {"workload": f"{count} 2D random-geometric graphs, n log-uniform [1e3, 2e6], mean degree 8, "
+                                  f"b = ceil(sqrt n), k in {{8,16,32,64}}, {iters} iterations, FP16 values and X",
+                      "rows": rows, "nnz": nnz, "sum_k_rows": sum(m.n * k for m, k in zip(mats16, ks)),
+                      "launches_per_step": 2 + iters, "prep_s": t_prep},
+           "aggregate_GBps": bytes16 / (ms_b / 1e3) / 1e9, "frac_of_measured_hbm": bytes16 / (ms_b / 1e3) / 1e9 / peak,
+           "fp32_one_launch_per_iteration": {"ms_per_step": ms_f, "matrix_iters_per_s": count * iters / (ms_f / 1e3),
+                                            "aggregate_GBps": bytes32 / (ms_f / 1e3) / 1e9,
+                                            "launches_per_step": count * (2 + iters)},
+           "speedup_vs_fp32": ms_f / ms_b, "max_normwise_err_f16_vs_f32": err, "peak_kind": peak_kind}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
+    if a.workload == "batch":
+        run_batch(a)
+        return
     spec = workload_spec(a)
     if a.impl == "reference":
         run_reference(a, spec)

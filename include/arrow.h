@@ -100,6 +100,19 @@ int arrow_upload(arrow_handle h);
  * Errors: ARROW_EINVAL, ARROW_ENOMEM, ARROW_ECUDA. */
 int arrow_handle_copy(arrow_handle h, int32_t value_dtype, arrow_handle* out);
 
+/* arrow_save -- write the handle's host state (input copy, every level's permutation and
+ * structure, the fused row program) to a binary file with a checksum, so that a
+ * decomposition computed once (the expensive offline step, Section 6) can be reused.
+ * Errors: ARROW_EINVAL (NULL, cannot write). */
+int arrow_save(arrow_handle h, const char* path);
+
+/* arrow_load -- read a file written by arrow_save.  o (may be NULL = as saved) overrides
+ * value_dtype (-1 keeps the saved one), flags (ARROW_HOST_ONLY) and device; the handle is
+ * uploaded unless host-only.
+ * Errors: ARROW_EINVAL (missing, truncated, corrupt or inconsistent file), ARROW_ENOMEM,
+ * ARROW_ECUDA. */
+int arrow_load(const char* path, const arrow_opts* o, arrow_handle* out);
+
 /* Release the handle and all host and device memory it owns.  NULL-safe.
  * Must not be called while work that uses the handle is still running on a stream. */
 void arrow_free(arrow_handle h);
@@ -185,6 +198,58 @@ int arrow_batch_status(arrow_batch b, int32_t* status);
 
 /* Release the batch (not its handles).  NULL-safe. */
 void arrow_batch_free(arrow_batch b);
+
+/* ---- serving: continuous batching of requests ---------------------------------------- */
+/* Not in the paper.  A request is (decomposed matrix, X, Y, k, iters); the server keeps the
+ * matrices and the requests' state on the device and advances every admitted request by one
+ * iteration per step, all of them in the same launches (continuous batching). */
+typedef struct arrow_server_s* arrow_server;   /* opaque, library-owned */
+
+typedef struct {
+    int64_t hbm_budget;    /* bytes of device memory for request state (allocated once, up front) */
+    int32_t max_active;    /* slots: requests advanced together, 1..4096                          */
+    int32_t x_dtype;       /* arrow_dtype of every request's X and Y                               */
+    int32_t max_inflight;  /* steps queued on the GPU before a step waits for the oldest; 0 = 2    */
+    int32_t device;        /* CUDA device ordinal; -1 = current                                    */
+} arrow_server_opts;
+
+typedef struct {
+    int64_t queued, active, inflight_steps, completed, steps;
+    int64_t bytes_in_use, peak_bytes;   /* request state in the budget (peak <= hbm_budget) */
+    int32_t status;                     /* device status word (0 = no wait ran out)          */
+} arrow_server_stats;
+
+/* Create a server; allocates hbm_budget bytes of device memory and a few pinned staging
+ * buffers.  Errors: ARROW_EINVAL (bad options), ARROW_ENOMEM, ARROW_ECUDA. */
+int arrow_server_create(const arrow_server_opts* o, arrow_server* out);
+
+/* Queue a request: Y = A^iters X for the uploaded handle h; X, Y DEVICE pointers (n x k,
+ * 16-byte aligned, caller-owned, valid until the request completes); k as for
+ * arrow_batch_spmm.  All handles served must store values in one dtype.  Its state needs
+ * 2 n k sizeof(x_dtype) + (split-row segments) k 4 bytes of the budget while active.
+ * *id identifies it in arrow_server_poll.  Errors: ARROW_EINVAL, ARROW_ESTATE. */
+int arrow_server_submit(arrow_server s, arrow_handle h, const void* X, void* Y, int64_t k, int32_t iters,
+                        int64_t* id);
+
+/* One step: retire requests the GPU has finished, admit queued requests in arrival order
+ * while a slot and budget are free, launch one iteration of every active request (plus the
+ * permute-in of new ones and the permute-out of finishing ones) on `stream`, which must be
+ * the same for every step.  Waits for the oldest step only when max_inflight steps are queued.
+ * *active receives the number of active requests (may be NULL).  Errors: ARROW_EINVAL, ARROW_ECUDA. */
+int arrow_server_step(arrow_server s, void* stream, int32_t* active);
+
+/* Completed requests since the last poll: up to max (id, latency = device completion time -
+ * submission time, seconds) pairs; *count receives how many.  Non-blocking. */
+int arrow_server_poll(arrow_server s, int64_t* ids, double* latency_s, int32_t max, int32_t* count);
+
+/* Step (on `stream`, as arrow_server_step) until every queued and active request has
+ * completed, then wait for the GPU. */
+int arrow_server_drain(arrow_server s, void* stream);
+
+int arrow_server_get_stats(arrow_server s, arrow_server_stats* st);
+
+/* Synchronise the server's stream and release everything it owns (not the handles).  NULL-safe. */
+void arrow_server_free(arrow_server s);
 
 /* ---- structure export (parity tests, reports) ------------------------------------ */
 /* Number of levels l (order of the decomposition). */

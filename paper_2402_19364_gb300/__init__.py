@@ -16,7 +16,7 @@ from ._native import (ARROW_BF16, ARROW_F16, ARROW_F32, ARROW_GRAPH, ARROW_HOST_
                       ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_PRED_BAND, ARROW_PRED_BLOCK, ARROW_PROFILE,
                       ARROW_RESCALE, ArrowError)
 
-__all__ = ["ArrowMatrix", "ArrowBatch", "ArrowError", "dtype_code", "ARROW_F32", "ARROW_BF16", "ARROW_F16"]
+__all__ = ["ArrowMatrix", "ArrowBatch", "ArrowServer", "ArrowError", "dtype_code", "ARROW_F32", "ARROW_BF16", "ARROW_F16"]
 
 _DTYPE_NAMES = {"f32": ARROW_F32, "float32": ARROW_F32, "bf16": ARROW_BF16, "bfloat16": ARROW_BF16,
                 "f16": ARROW_F16, "float16": ARROW_F16}
@@ -96,6 +96,26 @@ class ArrowMatrix:
 
     def __exit__(self, *exc):
         self.close()
+
+    def save(self, path) -> None:
+        """``arrow_save``: write the decomposition (host state) to ``path``."""
+        _native.check(_native.lib().arrow_save(self._h, str(path).encode()))
+
+    @classmethod
+    def load(cls, path, *, value_dtype=None, host_only: bool = False, device: int = -1) -> "ArrowMatrix":
+        """``arrow_load``: a handle from a file written by :meth:`save`."""
+        L = _native.lib()
+        o = _native.ArrowOpts()
+        _native.check(L.arrow_opts_default(ctypes.byref(o)))
+        o.value_dtype = -1 if value_dtype is None else dtype_code(value_dtype)
+        o.flags = ARROW_HOST_ONLY if host_only else 0
+        o.device = device
+        out = cls.__new__(cls)
+        out._h = ctypes.c_void_p()
+        _native.check(L.arrow_load(str(path).encode(), ctypes.byref(o), ctypes.byref(out._h)))
+        st = out.stats()
+        out.n, out.nnz, out.b, out.value_dtype = st["n"], st["nnz"], st["b"], st["value_dtype"]
+        return out
 
     def copy(self, value_dtype) -> "ArrowMatrix":
         """``arrow_handle_copy``: same decomposition, values stored in ``value_dtype``."""
@@ -243,6 +263,61 @@ class ArrowBatch:
         if getattr(self, "_b", None) and self._b.value:
             _native.lib().arrow_batch_free(self._b)
             self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ArrowServer:
+    """Continuous-batching server (``arrow_server_*``): submit requests, step, poll completions."""
+
+    def __init__(self, hbm_budget: int, max_active: int, x_dtype="bf16", max_inflight: int = 2, device: int = -1):
+        o = _native.ArrowServerOpts(int(hbm_budget), int(max_active), dtype_code(x_dtype), int(max_inflight),
+                                    int(device))
+        self._s = ctypes.c_void_p()
+        _native.check(_native.lib().arrow_server_create(ctypes.byref(o), ctypes.byref(self._s)))
+        self._keep = {}
+
+    def submit(self, M: ArrowMatrix, X, Y, iters: int) -> int:
+        """Queue Y = A^iters X (X, Y contiguous CUDA tensors kept alive until completion)."""
+        rid = ctypes.c_int64()
+        _native.check(_native.lib().arrow_server_submit(self._s, M._h, ctypes.c_void_p(X.data_ptr()),
+                                                        ctypes.c_void_p(Y.data_ptr()), int(X.shape[1]), int(iters),
+                                                        ctypes.byref(rid)))
+        self._keep[rid.value] = (M, X, Y)
+        return rid.value
+
+    def step(self, stream=None) -> int:
+        act = ctypes.c_int32()
+        _native.check(_native.lib().arrow_server_step(self._s, _stream_ptr(stream), ctypes.byref(act)))
+        return act.value
+
+    def poll(self, max_items: int = 4096):
+        """[(id, latency_seconds)] completed since the last poll."""
+        ids = (ctypes.c_int64 * max_items)()
+        lat = (ctypes.c_double * max_items)()
+        cnt = ctypes.c_int32()
+        _native.check(_native.lib().arrow_server_poll(self._s, ids, lat, max_items, ctypes.byref(cnt)))
+        out = [(ids[i], lat[i]) for i in range(cnt.value)]
+        for rid, _ in out:
+            self._keep.pop(rid, None)
+        return out
+
+    def drain(self, stream=None) -> None:
+        _native.check(_native.lib().arrow_server_drain(self._s, _stream_ptr(stream)))
+
+    def stats(self) -> dict:
+        st = _native.ArrowServerStats()
+        _native.check(_native.lib().arrow_server_get_stats(self._s, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_s", None) and self._s.value:
+            _native.lib().arrow_server_free(self._s)
+            self._s = ctypes.c_void_p()
 
     def __del__(self):
         try:

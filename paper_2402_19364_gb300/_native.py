@@ -48,6 +48,17 @@ class ArrowStats(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("decompose_seconds", ctypes.c_double)]
 
 
+class ArrowServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("max_active", ctypes.c_int32), ("x_dtype", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class ArrowServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("active", ctypes.c_int64), ("inflight_steps", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("steps", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64),
+                ("peak_bytes", ctypes.c_int64), ("status", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _I64 = ctypes.c_int64
@@ -60,10 +71,19 @@ SIGNATURES = {
     "arrow_upload": (_I32, [_P]),
     "arrow_free": (None, [_P]),
     "arrow_handle_copy": (_I32, [_P, _I32, ctypes.POINTER(_P)]),
+    "arrow_save": (_I32, [_P, ctypes.c_char_p]),
+    "arrow_load": (_I32, [ctypes.c_char_p, ctypes.POINTER(ArrowOpts), ctypes.POINTER(_P)]),
     "arrow_batch_create": (_I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)]),
     "arrow_batch_spmm": (_I32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64), _I32, _I32, _I32, _P]),
     "arrow_batch_status": (_I32, [_P, ctypes.POINTER(_I32)]),
     "arrow_batch_free": (None, [_P]),
+    "arrow_server_create": (_I32, [ctypes.POINTER(ArrowServerOpts), ctypes.POINTER(_P)]),
+    "arrow_server_submit": (_I32, [_P, _P, _P, _P, _I64, _I32, ctypes.POINTER(_I64)]),
+    "arrow_server_step": (_I32, [_P, _P, ctypes.POINTER(_I32)]),
+    "arrow_server_poll": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double), _I32, ctypes.POINTER(_I32)]),
+    "arrow_server_drain": (_I32, [_P, _P]),
+    "arrow_server_get_stats": (_I32, [_P, ctypes.POINTER(ArrowServerStats)]),
+    "arrow_server_free": (None, [_P]),
     "arrow_spmm": (_I32, [_P, _P, _I64, _I32, _P, _I32, _I32, _P]),
     "arrow_workspace_size": (_I32, [_P, _I64, _I32, _I32, ctypes.POINTER(_SIZE)]),
     "arrow_spmm_ws": (_I32, [_P, _P, _I64, _I32, _P, _I32, _I32, _P, _SIZE, _P]),

@@ -88,4 +88,7 @@ struct arrow_handle_s {
 namespace arrow {
 // Host decomposition (decompose.cpp).  Fills levels, entry_level and the fused row program.
 int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow_opts& o);
+// Serialisation of the host state (decompose.cpp).
+int save_host(const arrow_handle_s* h, const char* path);
+int load_host(arrow_handle_s* h, const char* path);
 }  // namespace arrow

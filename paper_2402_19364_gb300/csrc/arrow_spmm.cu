@@ -877,6 +877,42 @@ int arrow_upload(arrow_handle h) {
     return ARROW_OK;
 }
 
+int arrow_save(arrow_handle h, const char* path) {
+    if (!h || !path) { set_error("arrow_save: NULL argument"); return ARROW_EINVAL; }
+    return save_host(h, path);
+}
+
+int arrow_load(const char* path, const arrow_opts* o, arrow_handle* out) {
+    if (!out || !path) { set_error("arrow_load: NULL argument"); return ARROW_EINVAL; }
+    *out = nullptr;
+    arrow_handle_s* h = nullptr;
+    try {
+        h = new arrow_handle_s();
+        int rc = load_host(h, path);
+        if (rc != ARROW_OK) { delete h; return rc; }
+    } catch (const std::bad_alloc&) {
+        delete h;
+        set_error("arrow_load: host allocation failed");
+        return ARROW_ENOMEM;
+    }
+    if (o) {
+        if (o->value_dtype < -1 || o->value_dtype > ARROW_F16) {
+            delete h;
+            set_error("arrow_load: unknown value_dtype");
+            return ARROW_EINVAL;
+        }
+        if (o->value_dtype >= 0) h->opts.value_dtype = o->value_dtype;
+        h->opts.flags = o->flags;
+        h->opts.device = o->device;
+    }
+    if (!(h->opts.flags & ARROW_HOST_ONLY)) {
+        int rc = arrow_upload(h);
+        if (rc != ARROW_OK) { arrow_free(h); return rc; }
+    }
+    *out = h;
+    return ARROW_OK;
+}
+
 int arrow_handle_copy(arrow_handle h, int32_t value_dtype, arrow_handle* out) {
     if (!out) { set_error("arrow_handle_copy: out is NULL"); return ARROW_EINVAL; }
     *out = nullptr;

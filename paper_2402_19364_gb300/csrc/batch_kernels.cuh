@@ -1,0 +1,241 @@
+// Multi-matrix kernels shared by the batched path (arrow_batch.cu) and the serving runtime
+// (arrow_server.cu).  Work units of all matrices of a launch live in one index space: unit w
+// belongs to matrix m with base[m] <= w < base[m+1]; every matrix carries its own feature
+// width and ping-pong state, so a matrix computes the same bits whatever else shares the launch.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace arrow {
+
+struct MatDesc {
+    const int32_t* rowptr;
+    const int32_t* col;
+    const void* val;
+    const int32_t* tile_row;
+    const int32_t* tile_ent;
+    const int32_t* lcol;
+    const void* lval;
+    const int32_t* seg_begin;
+    const int32_t* seg_end;
+    const int32_t* long_rows;
+    const int32_t* long_segptr;
+    const int32_t* perm0;
+    const int32_t* iperm0;
+    const void* x_user;   // caller's X (vertex order)
+    void* y_user;         // caller's Y (vertex order)
+    void* xa;             // pi_0-ordered ping-pong buffers
+    void* xb;
+    float* partials;      // [n_seg][k]
+    int64_t n;
+    int64_t k;
+    int32_t T;            // lanes per row = k / V
+    int32_t flip;         // xor-ed into the launch parity (per-request ping-pong state)
+};
+
+struct BatchArgs {
+    const MatDesc* d;
+    const int64_t* base;   // [n_mats+1] prefix of this kernel class's work units
+    int32_t n_mats;
+    int64_t total;
+    int32_t parity;        // 0: xa -> xb, 1: xb -> xa
+    int32_t dir;           // gather: 0 permute-in, 1 permute-out
+    int32_t* status;
+};
+
+__device__ __forceinline__ int find_mat(const int64_t* base, int n, int64_t w) {
+    int lo = 0, hi = n - 1;   // largest m with base[m] <= w
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(base + mid) <= w) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int kBatchSmem = 128 + 2 * kBufBytes;
+
+// Rows of every matrix's tiles (the fused arrow-row kernel of arrow_spmm with a per-tile
+// matrix descriptor and a run-time team width).
+template <typename TX, typename TV>
+__global__ void __launch_bounds__(256, 3) arrow_batch_rows_kernel(BatchArgs a) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    constexpr int VE = 16 / int(sizeof(TV));
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    int* hdr = reinterpret_cast<int*>(smem + 16);     // per buffer: matrix, r0, r1, e0
+    unsigned char* bufs = smem + 128;
+    const int64_t G = gridDim.x;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t w, int b) {
+        const int m = find_mat(a.base, a.n_mats, w);
+        const MatDesc& d = a.d[m];
+        const int t = int(w - a.base[m]);
+        const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1], e0 = d.tile_ent[t], e1 = d.tile_ent[t + 1];
+        hdr[4 * b + 0] = m; hdr[4 * b + 1] = r0; hdr[4 * b + 2] = r1; hdr[4 * b + 3] = e0;
+        stage_tile<TV>(d.rowptr, d.col, static_cast<const TV*>(d.val), r0, r1, e0, e1, bufs + b * kBufBytes, &bar[b]);
+    };
+    if (threadIdx.x == 0) {
+        if (int64_t(blockIdx.x) < a.total) issue(blockIdx.x, 0);
+        if (int64_t(blockIdx.x) + G < a.total) issue(blockIdx.x + G, 1);
+    }
+    int i = 0;
+    int failed_at = -1;
+    for (int64_t w = blockIdx.x; w < a.total; w += G, ++i) {
+        const int b = i & 1;
+        unsigned char* buf = bufs + b * kBufBytes;
+        const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) { failed_at = i; break; }
+        const int m = hdr[4 * b + 0], r0 = hdr[4 * b + 1], r1 = hdr[4 * b + 2], e0 = hdr[4 * b + 3];
+        const MatDesc& d = a.d[m];
+        const int T = d.T;
+        const int teams = 256 / T;
+        const int team = threadIdx.x / T, tl = threadIdx.x & (T - 1);
+        const int64_t ldx = d.k;
+        const int par = a.parity ^ d.flip;
+        const TX* __restrict__ X = static_cast<const TX*>(par ? d.xb : d.xa) + tl * V;
+        TX* __restrict__ Y = static_cast<TX*>(par ? d.xa : d.xb) + tl * V;
+        const int32_t* srp = reinterpret_cast<const int32_t*>(buf) + (r0 & 3);
+        const int32_t* scol = reinterpret_cast<const int32_t*>(buf + kRpBytes) + (e0 & 3);
+        const TV* sval = reinterpret_cast<const TV*>(buf + kRpBytes + kColBytes) + (e0 & (VE - 1));
+        const int nrows = r1 - r0;
+        for (int j = team; j < nrows; j += teams) {
+            const int s = srp[j] - e0, e = srp[j + 1] - e0;
+            float acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = 0.f;
+            for (int base = s; base < e; base += 8) {
+                const int cnt = e - base;
+                uint4 x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (u < cnt) x[u] = ld_x(X + int64_t(scol[base + u]) * ldx);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (u < cnt) {
+                        const float wv = val_to_float(sval[base + u]);
+                        float f[V];
+                        P::to_float(x[u], f);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = fmaf(wv, f[v], acc[v]);
+                    }
+                }
+            }
+            *reinterpret_cast<uint4*>(Y + int64_t(r0 + j) * ldx) = P::from_float(acc);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && w + 2 * G < a.total) issue(w + 2 * G, b);
+    }
+    if (failed_at >= 0 && threadIdx.x == 0) {
+        atomicExch(a.status, kStatusTimeout);
+        mbar_wait_bounded(&bar[failed_at & 1], (failed_at >> 1) & 1, kWaitLimitNs);
+        if (int64_t(blockIdx.x) + int64_t(failed_at + 1) * G < a.total)
+            mbar_wait_bounded(&bar[(failed_at + 1) & 1], ((failed_at + 1) >> 1) & 1, kWaitLimitNs);
+    }
+}
+
+// One warp per split-row segment of any matrix (first stage of the head-row reduction).
+template <typename TX, typename TV>
+__global__ void __launch_bounds__(256) arrow_batch_segments_kernel(BatchArgs a) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t w = warp0; w < a.total; w += nwarps) {
+        const int m = find_mat(a.base, a.n_mats, w);
+        const MatDesc& d = a.d[m];
+        const int64_t g = w - a.base[m];
+        const int T = d.T, tpw = 32 / T, tl = lane & (T - 1), tw = lane / T;
+        const TX* __restrict__ X = static_cast<const TX*>((a.parity ^ d.flip) ? d.xb : d.xa) + tl * V;
+        const TV* __restrict__ val = static_cast<const TV*>(d.lval);
+        const int32_t s = __ldg(d.seg_begin + g), e = __ldg(d.seg_end + g);
+        float acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.f;
+        for (int32_t j = s + tw; j < e; j += tpw) {
+            const int32_t c = ld_stream_i32(d.lcol + j);
+            const float wv = val_to_float(ld_stream_val<TV>(val + j));
+            float f[V];
+            P::to_float(ld_x(X + int64_t(c) * d.k), f);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = fmaf(wv, f[v], acc[v]);
+        }
+        for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+        if (tw == 0) {
+            float4* p = reinterpret_cast<float4*>(d.partials + g * d.k + tl * V);
+#pragma unroll
+            for (int q = 0; q < V / 4; ++q) p[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+    }
+}
+
+// One warp per split row of any matrix: its segment partials in segment order (second stage).
+template <typename TX>
+__global__ void __launch_bounds__(256) arrow_batch_combine_kernel(BatchArgs a) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t w = warp0; w < a.total; w += nwarps) {
+        const int m = find_mat(a.base, a.n_mats, w);
+        const MatDesc& d = a.d[m];
+        const int64_t li = w - a.base[m];
+        if (lane >= d.T) continue;
+        float acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.f;
+        const int g0 = __ldg(d.long_segptr + li), g1 = __ldg(d.long_segptr + li + 1);
+        for (int g = g0; g < g1; ++g) {
+            const float4* p = reinterpret_cast<const float4*>(d.partials + int64_t(g) * d.k + lane * V);
+#pragma unroll
+            for (int q = 0; q < V / 4; ++q) {
+                const float4 f = p[q];
+                acc[4 * q + 0] += f.x; acc[4 * q + 1] += f.y; acc[4 * q + 2] += f.z; acc[4 * q + 3] += f.w;
+            }
+        }
+        TX* Y = static_cast<TX*>((a.parity ^ d.flip) ? d.xa : d.xb);
+        *reinterpret_cast<uint4*>(Y + int64_t(__ldg(d.long_rows + li)) * d.k + lane * V) = P::from_float(acc);
+    }
+}
+
+// Permute-in (dir 0: xa[p] = X[pi_0^{-1}(p)]) or permute-out (dir 1: Y[v] = buf[pi_0(v)], buf =
+// xa or xb by parity) of every matrix; a warp per chunk of 32 rows.
+template <typename TX>
+__global__ void __launch_bounds__(256) arrow_batch_gather_kernel(BatchArgs a) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t w = warp0; w < a.total; w += nwarps) {
+        const int m = find_mat(a.base, a.n_mats, w);
+        const MatDesc& d = a.d[m];
+        const int64_t c = w - a.base[m];
+        const int nv = d.T, rpw = 32 / nv, lr = lane / nv, lq = lane - lr * nv;
+        const TX* src;
+        TX* dst;
+        const int32_t* idx;
+        if (a.dir == 0) {
+            src = static_cast<const TX*>(d.x_user); dst = static_cast<TX*>(d.xa); idx = d.iperm0;
+        } else {
+            src = static_cast<const TX*>((a.parity ^ d.flip) ? d.xb : d.xa); dst = static_cast<TX*>(d.y_user);
+            idx = d.perm0;
+        }
+        const int64_t r_end = min(d.n, (c + 1) * 32);
+        for (int64_t r = c * 32 + lr; r < r_end; r += rpw) {
+            const int64_t s = __ldg(idx + r);
+            *reinterpret_cast<uint4*>(dst + r * d.k + lq * V) = ld_x(src + s * d.k + lq * V);
+        }
+    }
+}
+
+}  // namespace arrow

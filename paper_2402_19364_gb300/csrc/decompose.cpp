@@ -629,3 +629,141 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
 }
 
 }  // namespace arrow
+
+// ---------------------------------------------------------------------------------------
+// Serialisation of a decomposed handle (host state only; the device copy is rebuilt by
+// arrow_upload).  Little-endian binary: magic, version, scalars, the levels' permutations,
+// every host array with an int64 length prefix, and an FNV-1a 64 checksum of all of it.
+// ---------------------------------------------------------------------------------------
+#include <cstdio>
+
+namespace arrow {
+namespace {
+
+constexpr char kMagic[8] = {'A', 'R', 'W', 'D', 'E', 'C', '1', '\0'};
+constexpr int64_t kVersion = 1;
+
+struct Writer {
+    FILE* f;
+    uint64_t h = 1469598103934665603ull;
+    bool ok = true;
+    void raw(const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+        if (n && std::fwrite(p, 1, n, f) != n) ok = false;
+    }
+    template <class T> void val(const T& v) { raw(&v, sizeof(T)); }
+    template <class T> void vec(const std::vector<T>& v) {
+        val(int64_t(v.size()));
+        raw(v.data(), v.size() * sizeof(T));
+    }
+};
+
+struct Reader {
+    FILE* f;
+    uint64_t h = 1469598103934665603ull;
+    bool ok = true;
+    void raw(void* p, size_t n) {
+        if (n && std::fread(p, 1, n, f) != n) { ok = false; return; }
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+    }
+    template <class T> void val(T& v) { raw(&v, sizeof(T)); }
+    template <class T> void vec(std::vector<T>& v, int64_t max_len) {
+        int64_t n = -1;
+        val(n);
+        if (!ok || n < 0 || n > max_len) { ok = false; return; }
+        v.resize(size_t(n));
+        raw(v.data(), size_t(n) * sizeof(T));
+    }
+};
+
+}  // namespace
+
+int save_host(const arrow_handle_s* h, const char* path) {
+    FILE* f = std::fopen(path, "wb");
+    if (!f) { set_error(std::string("arrow_save: cannot open ") + path); return ARROW_EINVAL; }
+    Writer w{f};
+    w.raw(kMagic, 8);
+    w.val(kVersion);
+    w.val(h->n); w.val(h->nnz); w.val(h->b);
+    w.val(h->opts);
+    w.val(h->long_row);
+    w.val(h->decompose_seconds);
+    w.val(int64_t(h->levels.size()));
+    for (const Level& l : h->levels) {
+        w.val(l.n_active);
+        w.val(l.nnz);
+        w.vec(l.perm);
+    }
+    w.vec(h->rowptr); w.vec(h->colidx); w.vec(h->values); w.vec(h->entry_level);
+    w.vec(h->f_rowptr); w.vec(h->f_col); w.vec(h->f_src); w.vec(h->l_col); w.vec(h->l_src);
+    w.vec(h->long_rows); w.vec(h->long_segptr); w.vec(h->seg_begin); w.vec(h->seg_end);
+    w.vec(h->tile_row); w.vec(h->tile_ent);
+    const uint64_t sum = w.h;
+    if (std::fwrite(&sum, sizeof(sum), 1, f) != 1) w.ok = false;
+    if (std::fclose(f) != 0) w.ok = false;
+    if (!w.ok) { set_error(std::string("arrow_save: write failed for ") + path); return ARROW_EINVAL; }
+    return ARROW_OK;
+}
+
+int load_host(arrow_handle_s* h, const char* path) {
+    FILE* f = std::fopen(path, "rb");
+    if (!f) { set_error(std::string("arrow_load: cannot open ") + path); return ARROW_EINVAL; }
+    Reader r{f};
+    char magic[8];
+    int64_t version = 0, nl = -1;
+    r.raw(magic, 8);
+    r.val(version);
+    if (!r.ok || std::memcmp(magic, kMagic, 8) != 0 || version != kVersion) {
+        std::fclose(f);
+        set_error("arrow_load: not an arrow decomposition file (magic/version)");
+        return ARROW_EINVAL;
+    }
+    r.val(h->n); r.val(h->nnz); r.val(h->b);
+    r.val(h->opts);
+    r.val(h->long_row);
+    r.val(h->decompose_seconds);
+    r.val(nl);
+    const int64_t n = h->n, nnz = h->nnz;
+    if (!r.ok || n < 0 || n >= (int64_t(1) << 31) || nnz < 0 || nnz >= (int64_t(1) << 31) || nl < 0 || nl > 254) {
+        std::fclose(f);
+        set_error("arrow_load: corrupt header");
+        return ARROW_EINVAL;
+    }
+    h->levels.resize(size_t(nl));
+    for (Level& l : h->levels) {
+        r.val(l.n_active);
+        r.val(l.nnz);
+        r.vec(l.perm, n);
+    }
+    r.vec(h->rowptr, n + 1); r.vec(h->colidx, nnz); r.vec(h->values, nnz); r.vec(h->entry_level, nnz);
+    r.vec(h->f_rowptr, n + 1); r.vec(h->f_col, nnz); r.vec(h->f_src, nnz); r.vec(h->l_col, nnz); r.vec(h->l_src, nnz);
+    r.vec(h->long_rows, n); r.vec(h->long_segptr, n + 1); r.vec(h->seg_begin, nnz + 1); r.vec(h->seg_end, nnz + 1);
+    r.vec(h->tile_row, n + 2); r.vec(h->tile_ent, n + 2);
+    const uint64_t want = r.h;
+    uint64_t sum = 0;
+    const bool got = std::fread(&sum, sizeof(sum), 1, f) == 1;
+    std::fclose(f);
+    if (!r.ok || !got || sum != want) {
+        set_error("arrow_load: truncated or corrupt file (checksum)");
+        return ARROW_EINVAL;
+    }
+    // structural consistency of what the device path will index
+    bool bad = int64_t(h->rowptr.size()) != n + 1 || int64_t(h->f_rowptr.size()) != (n ? n + 1 : h->f_rowptr.size()) ||
+               h->f_col.size() != h->f_src.size() || h->l_col.size() != h->l_src.size() ||
+               h->seg_begin.size() != h->seg_end.size() || h->tile_row.size() != h->tile_ent.size();
+    for (const Level& l : h->levels) bad = bad || int64_t(l.perm.size()) != n;
+    for (int32_t c : h->f_col) bad = bad || c < 0 || c >= n;
+    for (int32_t c : h->l_col) bad = bad || c < 0 || c >= n;
+    for (int32_t s : h->f_src) bad = bad || s < 0 || s >= nnz;
+    for (int32_t s : h->l_src) bad = bad || s < 0 || s >= nnz;
+    if (!bad && !h->f_rowptr.empty()) bad = h->f_rowptr.back() != int32_t(h->f_col.size());
+    if (bad) {
+        set_error("arrow_load: inconsistent arrays");
+        return ARROW_EINVAL;
+    }
+    return ARROW_OK;
+}
+
+}  // namespace arrow

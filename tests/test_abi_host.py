@@ -152,3 +152,31 @@ def test_fused_program_stats(arrow):
     assert s["long_rows"] == int((deg > 32).sum())
     assert s["segments"] == int(np.sum((deg[deg > 32] + 63) // 64))
     assert s["tiles"] >= (A.n + 255) // 256
+
+
+def test_save_load_roundtrip_and_corruption(arrow, tmp_path):
+    from paper_2402_19364_gb300 import _native
+    A = w.rmat_gcn(11, 16, seed=4)
+    M = arrow.ArrowMatrix(A, 64, seed=3, host_only=True, long_row=16)
+    p = tmp_path / "m.arw"
+    M.save(p)
+    L2 = arrow.ArrowMatrix.load(p, host_only=True)
+    assert L2.num_levels == M.num_levels and L2.stats()["segments"] == M.stats()["segments"]
+    for i in range(M.num_levels):
+        assert np.array_equal(L2.level_perm(i), M.level_perm(i))
+        assert L2.level_info(i) == M.level_info(i)
+        for x, y in zip(L2.level_csr(i), M.level_csr(i)):
+            assert np.array_equal(x, y)
+    raw = bytearray(p.read_bytes())
+    raw[len(raw) // 2] ^= 0xFF                                   # flip a byte: checksum fails
+    bad = tmp_path / "bad.arw"
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(arrow.ArrowError) as e:
+        arrow.ArrowMatrix.load(bad, host_only=True)
+    assert e.value.code == _native.ARROW_EINVAL
+    short = tmp_path / "short.arw"
+    short.write_bytes(p.read_bytes()[:1000])                      # truncated
+    with pytest.raises(arrow.ArrowError):
+        arrow.ArrowMatrix.load(short, host_only=True)
+    with pytest.raises(arrow.ArrowError):
+        arrow.ArrowMatrix.load(tmp_path / "missing.arw", host_only=True)

@@ -195,6 +195,19 @@ def test_status_word_and_bounded_wait_selftest(arrow):
     assert torch.allclose(Y, torch.ones_like(Y), atol=1e-5)
 
 
+def test_saved_handle_gives_same_bits(arrow, tmp_path):
+    A = w.rmat_gcn(11, 16, seed=2)
+    M = arrow.ArrowMatrix(A, 64, long_row=32)
+    M.save(tmp_path / "a.arw")
+    L = arrow.ArrowMatrix.load(tmp_path / "a.arw")
+    X = torch.from_numpy(w.features(A.n, 32, seed=5)).cuda()
+    assert torch.equal(M.spmm(X, 4), L.spmm(X, 4))
+    Lb = arrow.ArrowMatrix.load(tmp_path / "a.arw", value_dtype="bf16")
+    Yb = Lb.spmm(X.bfloat16(), 4).float()
+    Yf = M.spmm(X, 4)
+    assert float(torch.linalg.vector_norm(Yb - Yf) / torch.linalg.vector_norm(Yf)) < 2e-2
+
+
 # ---- full-size workloads (the launch configuration bench.py times) -----------------------
 
 def _sample_rows(n, count, seed):
