@@ -96,7 +96,7 @@ void enqueue(arrow_batch_s* B, int x_dtype, int iters, cudaStream_t s) {
 
 template <typename TX, typename TV>
 void set_attrs_typed() {
-    cudaFuncSetAttribute(arrow_batch_rows_kernel<TX, TV>, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
+    prepare_batch_rows<TX, TV>();
 }
 
 void set_attrs(int x_dtype, int v_dtype) {

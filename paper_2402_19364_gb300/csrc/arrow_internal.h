@@ -14,8 +14,14 @@ void set_error(const std::string& msg);
 
 // Row tiles of the fused row program: at most kTileRows rows and kTileNnz entries each.
 // A tile's row pointers and entries are staged into shared memory with bulk copies.
-constexpr int kTileRows = 256;
-constexpr int kTileNnz = 2048;
+#ifndef ARROW_TILE_NNZ
+#define ARROW_TILE_NNZ 2048
+#endif
+#ifndef ARROW_TILE_ROWS
+#define ARROW_TILE_ROWS 256
+#endif
+constexpr int kTileRows = ARROW_TILE_ROWS;
+constexpr int kTileNnz = ARROW_TILE_NNZ;
 constexpr int kDefaultLongRow = 64;
 constexpr int kDefaultSegment = 512;
 

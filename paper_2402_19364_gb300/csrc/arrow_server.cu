@@ -146,6 +146,7 @@ void launch_step(arrow_server_s* S, const int64_t* tot, int n_m, cudaStream_t s)
     if (tot[0]) arrow_batch_gather_kernel<TX><<<grid_w(tot[0], 8), 256, 0, s>>>(args(0, 0, 0));
     if (tot[1]) arrow_batch_segments_kernel<TX, TV><<<grid_w(tot[1], 8), 256, 0, s>>>(args(1, 0, 0));
     if (tot[2]) {
+        prepare_batch_rows<TX, TV>();
         const int g = int(std::max<int64_t>(1, std::min<int64_t>(tot[2], int64_t(sm) * 3)));
         arrow_batch_rows_kernel<TX, TV><<<g, 256, kBatchSmem, s>>>(args(2, 0, 0));
     }

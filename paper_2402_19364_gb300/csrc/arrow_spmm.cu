@@ -51,7 +51,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 // kernels
 // ------------------------------------------------------------------------------------
 // + per-warp FP64 column sums of squares (8 warps x kc doubles) after the two buffers
-constexpr int kRowsSmemBase = 128 + 2 * kBufBytes;
+constexpr int kRowsSmemBase = 128 + kStages * kBufBytes;
 static inline int rows_smem_bytes(int kc) { return kRowsSmemBase + 8 * kc * 8; }
 
 struct RowArgs {
@@ -79,21 +79,25 @@ __device__ __forceinline__ void issue_tile(const RowArgs& a, int t, unsigned cha
 }
 
 // Fused arrow-row kernel (persistent).  Each CTA walks row tiles t = blockIdx.x, +gridDim.x,
-// ...; a tile's row pointers and entries arrive by bulk copy, two tiles in flight.  A team
-// of T lanes owns a row: it reads up to 8 entries from shared memory, issues their 16-byte
-// X gathers together, accumulates in FP32 in entry order (levels in order), scales,
-// stores the row and, with RESCALE, adds its squares to FP64 per-column partials.
+// ...; a tile's row pointers and entries arrive by bulk copy into one of kStages buffers.
+// Warps are not synchronised per tile: every warp takes its rows of the tile as soon as the
+// tile has landed, and the last warp done with a buffer re-arms it with the tile kStages
+// ahead.  A team of T lanes owns a row: it reads up to 8 entries from shared memory, issues
+// their 16-byte X gathers together, accumulates in FP32 in entry order (levels in order),
+// scales, stores the row and, with RESCALE, adds its squares to FP64 per-column sums.
 template <typename TX, typename TV, int T, bool RESCALE>
 __global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(RowArgs a) {
     using P = Pack<TX>;
     constexpr int V = P::V;
     constexpr int VE = 16 / int(sizeof(TV));
     constexpr int TEAMS = 256 / T;
+    constexpr int NW = 8;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    PipeSmem* ps = reinterpret_cast<PipeSmem*>(smem);
     unsigned char* bufs = smem + 128;
     double* wsum = reinterpret_cast<double*>(smem + kRowsSmemBase);   // [8][kc]
     const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const int tl = threadIdx.x & (T - 1);
     const int team = threadIdx.x / T;
     const int col0 = tl * V;
@@ -102,17 +106,23 @@ __global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(
     const int G = gridDim.x;
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < kStages; ++b) {
+            mbar_init(&ps->full[b], 1);
+            ps->done[b] = 0;
+            ps->issued[b] = 0;
+        }
+        ps->failed = 0;
         fence_mbar_init();
     }
     if (RESCALE)
         for (int c = threadIdx.x; c < 8 * a.kc; c += blockDim.x) wsum[c] = 0.0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (int(blockIdx.x) < a.n_tiles) issue_tile<TV>(a, blockIdx.x, bufs, &bar[0]);
-        if (int(blockIdx.x) + G < a.n_tiles) issue_tile<TV>(a, blockIdx.x + G, bufs + kBufBytes, &bar[1]);
-    }
+    if (threadIdx.x == 0)
+        for (int b = 0; b < kStages; ++b)
+            if (int(blockIdx.x) + b * G < a.n_tiles) {
+                issue_tile<TV>(a, blockIdx.x + b * G, bufs + b * kBufBytes, &ps->full[b]);
+                ps->issued[b]++;
+            }
     float scl[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) scl[v] = a.scale ? float(a.scale[a.koff + col0 + v]) : 1.0f;
@@ -121,12 +131,14 @@ __global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(
     for (int v = 0; v < V; ++v) sq[v] = 0.f;
 
     int i = 0;
-    int failed_at = -1;
     for (int t = blockIdx.x; t < a.n_tiles; t += G, ++i) {
-        const int b = i & 1;
+        const int b = i % kStages;
         unsigned char* buf = bufs + b * kBufBytes;
-        const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, kWaitLimitNs);
-        if (__syncthreads_or(!ok)) { failed_at = i; break; }
+        const bool ok = mbar_wait_bounded(&ps->full[b], (i / kStages) & 1, kWaitLimitNs);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (lane == 0) { ps->failed = 1; atomicExch(a.status, kStatusTimeout); }
+            break;
+        }
         const int r0 = __ldg(a.tile_row + t), r1 = __ldg(a.tile_row + t + 1), e0 = __ldg(a.tile_ent + t);
         const int32_t* srp = reinterpret_cast<const int32_t*>(buf) + (r0 & 3);
         const int32_t* scol = reinterpret_cast<const int32_t*>(buf + kRpBytes) + (e0 & 3);
@@ -174,26 +186,27 @@ __global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(
                 for (int v = 0; v < V; ++v) sq[v] += __shfl_xor_sync(0xffffffffu, sq[v], off);
             if (lane < T)
 #pragma unroll
-                for (int v = 0; v < V; ++v) wsum[(threadIdx.x >> 5) * a.kc + col0 + v] += double(sq[v]);
+                for (int v = 0; v < V; ++v) wsum[warp * a.kc + col0 + v] += double(sq[v]);
 #pragma unroll
             for (int v = 0; v < V; ++v) sq[v] = 0.f;
         }
-        __syncthreads();   // every thread is done with buf
-        if (threadIdx.x == 0 && t + 2 * G < a.n_tiles) issue_tile<TV>(a, t + 2 * G, buf, &bar[b]);
+        __syncwarp();
+        if (lane == 0)
+            release_buffer(ps, b, NW, [&](int bb) {
+                const int tn = t + kStages * G;
+                if (tn < a.n_tiles) {
+                    issue_tile<TV>(a, tn, bufs + bb * kBufBytes, &ps->full[bb]);
+                    ps->issued[bb]++;
+                }
+            });
     }
-    if (failed_at >= 0) {
-        // a staged tile never arrived: report, wait (bounded) for copies still in flight, leave
-        if (threadIdx.x == 0) {
-            atomicExch(a.status, kStatusTimeout);
-            const int t = blockIdx.x + failed_at * G;
-            mbar_wait_bounded(&bar[failed_at & 1], (failed_at >> 1) & 1, kWaitLimitNs);
-            if (t + G < a.n_tiles) mbar_wait_bounded(&bar[(failed_at + 1) & 1], ((failed_at + 1) >> 1) & 1, kWaitLimitNs);
-        }
+    __syncthreads();
+    if (ps->failed) {
+        if (threadIdx.x == 0) drain_pipeline(ps);
         return;
     }
     if (RESCALE) {
         // block's FP64 column sums: warps in fixed order
-        __syncthreads();
         for (int c = threadIdx.x; c < a.kc; c += blockDim.x) {
             double acc = 0.0;
             for (int w = 0; w < 8; ++w) acc += wsum[w * a.kc + c];

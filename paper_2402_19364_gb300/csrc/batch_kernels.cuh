@@ -52,46 +52,53 @@ __device__ __forceinline__ int find_mat(const int64_t* base, int n, int64_t w) {
     return lo;
 }
 
-constexpr int kBatchSmem = 128 + 2 * kBufBytes;
+constexpr int kBatchSmem = 128 + kStages * kBufBytes;
 
 // Rows of every matrix's tiles (the fused arrow-row kernel of arrow_spmm with a per-tile
-// matrix descriptor and a run-time team width).
+// matrix descriptor and a run-time team width); same tile pipeline without block barriers.
 template <typename TX, typename TV>
 __global__ void __launch_bounds__(256, 3) arrow_batch_rows_kernel(BatchArgs a) {
     using P = Pack<TX>;
     constexpr int V = P::V;
     constexpr int VE = 16 / int(sizeof(TV));
+    constexpr int NW = 8;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    int* hdr = reinterpret_cast<int*>(smem + 16);     // per buffer: matrix, r0, r1, e0
+    PipeSmem* ps = reinterpret_cast<PipeSmem*>(smem);
     unsigned char* bufs = smem + 128;
+    const int lane = threadIdx.x & 31;
     const int64_t G = gridDim.x;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
     auto issue = [&](int64_t w, int b) {
         const int m = find_mat(a.base, a.n_mats, w);
         const MatDesc& d = a.d[m];
         const int t = int(w - a.base[m]);
         const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1], e0 = d.tile_ent[t], e1 = d.tile_ent[t + 1];
-        hdr[4 * b + 0] = m; hdr[4 * b + 1] = r0; hdr[4 * b + 2] = r1; hdr[4 * b + 3] = e0;
-        stage_tile<TV>(d.rowptr, d.col, static_cast<const TV*>(d.val), r0, r1, e0, e1, bufs + b * kBufBytes, &bar[b]);
+        ps->hdr[b][0] = m; ps->hdr[b][1] = r0; ps->hdr[b][2] = r1; ps->hdr[b][3] = e0;
+        stage_tile<TV>(d.rowptr, d.col, static_cast<const TV*>(d.val), r0, r1, e0, e1, bufs + b * kBufBytes, &ps->full[b]);
+        ps->issued[b]++;
     };
     if (threadIdx.x == 0) {
-        if (int64_t(blockIdx.x) < a.total) issue(blockIdx.x, 0);
-        if (int64_t(blockIdx.x) + G < a.total) issue(blockIdx.x + G, 1);
+        for (int b = 0; b < kStages; ++b) {
+            mbar_init(&ps->full[b], 1);
+            ps->done[b] = 0;
+            ps->issued[b] = 0;
+        }
+        ps->failed = 0;
+        fence_mbar_init();
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int b = 0; b < kStages; ++b)
+            if (int64_t(blockIdx.x) + b * G < a.total) issue(blockIdx.x + b * G, b);
     int i = 0;
-    int failed_at = -1;
     for (int64_t w = blockIdx.x; w < a.total; w += G, ++i) {
-        const int b = i & 1;
+        const int b = i % kStages;
         unsigned char* buf = bufs + b * kBufBytes;
-        const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, kWaitLimitNs);
-        if (__syncthreads_or(!ok)) { failed_at = i; break; }
-        const int m = hdr[4 * b + 0], r0 = hdr[4 * b + 1], r1 = hdr[4 * b + 2], e0 = hdr[4 * b + 3];
+        const bool ok = mbar_wait_bounded(&ps->full[b], (i / kStages) & 1, kWaitLimitNs);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (lane == 0) { ps->failed = 1; atomicExch(a.status, kStatusTimeout); }
+            break;
+        }
+        const int m = ps->hdr[b][0], r0 = ps->hdr[b][1], r1 = ps->hdr[b][2], e0 = ps->hdr[b][3];
         const MatDesc& d = a.d[m];
         const int T = d.T;
         const int teams = 256 / T;
@@ -128,15 +135,30 @@ __global__ void __launch_bounds__(256, 3) arrow_batch_rows_kernel(BatchArgs a) {
             }
             *reinterpret_cast<uint4*>(Y + int64_t(r0 + j) * ldx) = P::from_float(acc);
         }
-        __syncthreads();
-        if (threadIdx.x == 0 && w + 2 * G < a.total) issue(w + 2 * G, b);
+        __syncwarp();
+        if (lane == 0)
+            release_buffer(ps, b, NW, [&](int bb) {
+                const int64_t wn = w + kStages * G;
+                if (wn < a.total) issue(wn, bb);
+            });
     }
-    if (failed_at >= 0 && threadIdx.x == 0) {
-        atomicExch(a.status, kStatusTimeout);
-        mbar_wait_bounded(&bar[failed_at & 1], (failed_at >> 1) & 1, kWaitLimitNs);
-        if (int64_t(blockIdx.x) + int64_t(failed_at + 1) * G < a.total)
-            mbar_wait_bounded(&bar[(failed_at + 1) & 1], ((failed_at + 1) >> 1) & 1, kWaitLimitNs);
-    }
+    __syncthreads();
+    if (ps->failed && threadIdx.x == 0) drain_pipeline(ps);
+}
+
+#ifndef ARROW_ROWS_CARVEOUT
+#define ARROW_ROWS_CARVEOUT 50
+#endif
+// Opt the batched rows kernel into its dynamic shared memory (more than the 48 KB default)
+// and set its carveout; once per instantiation and translation unit.
+template <typename TX, typename TV>
+inline void prepare_batch_rows() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(arrow_batch_rows_kernel<TX, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
+    cudaFuncSetAttribute(arrow_batch_rows_kernel<TX, TV>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         ARROW_ROWS_CARVEOUT);
+    done = true;
 }
 
 // One warp per split-row segment of any matrix (first stage of the head-row reduction).

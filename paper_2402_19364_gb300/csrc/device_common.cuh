@@ -137,12 +137,53 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
 constexpr int kStatusTimeout = 1;
 
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Shared-memory layout of one staged tile: row pointers, column indices, values, each a
 // 16-byte aligned superset of the tile's range.
 constexpr int kRpBytes = ((kTileRows + 1 + 6) * 4 + 15) / 16 * 16;
 constexpr int kColBytes = ((kTileNnz + 8) * 4 + 15) / 16 * 16;
 constexpr int kValBytes = kColBytes;
 constexpr int kBufBytes = (kRpBytes + kColBytes + kValBytes + 127) / 128 * 128;
+
+// Tile pipeline state at the start of dynamic shared memory (128 bytes): one "full"
+// mbarrier per staging buffer (completed by the buffer's bulk copies), the number of warps
+// done with the buffer's current use, the buffer's issued uses, and a small header.
+#ifndef ARROW_STAGES
+#define ARROW_STAGES 2
+#endif
+constexpr int kStages = ARROW_STAGES;
+struct PipeSmem {
+    uint64_t full[kStages];
+    int done[kStages];
+    int issued[kStages];
+    int hdr[kStages][4];
+    int failed;
+};
+static_assert(sizeof(PipeSmem) <= 128, "pipeline state must fit in 128 bytes");
+
+// Called by lane 0 of every warp when the warp is done with the tile in buffer b: the last
+// warp to finish re-arms the buffer by calling issue(b) (after ordering the warps' shared
+// memory reads before the asynchronous writes).  Returns nothing; no block-wide barrier.
+template <class Issue>
+__device__ __forceinline__ void release_buffer(PipeSmem* ps, int b, int nwarps, Issue&& issue) {
+    __threadfence_block();
+    if (atomicAdd(&ps->done[b], 1) == nwarps - 1) {
+        ps->done[b] = 0;
+        __threadfence_block();
+        fence_proxy_async_smem();
+        issue(b);
+    }
+}
+
+// After a failed wait: bounded waits for the latest issued use of every buffer (earlier uses
+// completed before the buffer was re-armed), so no copy is left in flight.
+__device__ __forceinline__ void drain_pipeline(PipeSmem* ps) {
+    for (int b = 0; b < kStages; ++b)
+        if (ps->issued[b] > 0) mbar_wait_bounded(&ps->full[b], uint32_t((ps->issued[b] - 1) & 1), kWaitLimitNs);
+}
 
 // Stage the row tile [r0, r1) with entries [e0, e1) into buf: row pointers, columns and values,
 // each as a 16-byte aligned superset (the arrays are padded by 64 bytes), completing on bar.
