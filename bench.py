@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="grid3d", choices=["grid3d", "grid2d", "rmat", "batch"])
+    p.add_argument("--workload", default="grid3d", choices=["grid3d", "grid2d", "rmat", "batch", "serve"])
     p.add_argument("--count", type=int, default=0, help="matrices of the batch workload (0 = 512)")
     p.add_argument("--size", type=int, default=0, help="grid side / R-MAT scale (0 = workload default)")
     p.add_argument("--iters", type=int, default=0)
@@ -326,10 +326,128 @@ def run_batch(a):
     print(json.dumps(out), flush=True)
 
 
+def _pool_worker(task):
+    """Spawned worker: generate one matrix of the serving pool, decompose it, save it."""
+    i, fam, n, seed, path = task
+    import workloads as w
+    import paper_2402_19364_gb300 as arrow
+    if fam == "grid":
+        N = max(8, int(round(n ** (1 / 3))))
+        A = w.grid_stencil((N, N, N), seed=seed)
+    elif fam == "rgg":
+        A = w.rgg(int(n), seed=seed, round_to=None)
+    else:
+        A = w.rmat_gcn(max(10, int(round(math.log2(n)))), 16, seed=seed)
+    b = int(math.ceil(math.sqrt(A.n)))
+    M = arrow.ArrowMatrix(A, b, host_only=True, nthreads=4, value_dtype="bf16")
+    M.save(path)
+    return i, fam, A.n, A.nnz
+
+
+def run_serve(a):
+    """Serving workload: Poisson arrivals of requests on a pool of pre-decomposed matrices
+    (grid / random-geometric / R-MAT, n log-uniform in [1e4, 8e6]), k in {16,32,64,128} BF16,
+    iterations uniform in [5, 50]; continuous batching with admission by HBM footprint.
+    Reports closed-loop capacity, then p50/p99 latency and throughput at 0.5, 0.8, 0.95 of it."""
+    import multiprocessing as mp
+    import tempfile
+    import torch
+    import workloads as w
+    from paper_2402_19364_gb300 import build as _build
+    _build.build()
+    import paper_2402_19364_gb300 as arrow
+    per_family = 6
+    fams = ["grid", "rgg", "rmat"]
+    sizes = w.log_uniform_sizes(per_family * 3, 1e4, 8e6, 11)
+    tmp = tempfile.mkdtemp(prefix="arrow_pool_", dir="/dev/shm" if os.path.isdir("/dev/shm") else None)
+    tasks = [(i, fams[i % 3], int(sizes[i]), 100 + i, os.path.join(tmp, f"p{i}.arw")) for i in range(per_family * 3)]
+    t0 = time.perf_counter()
+    info = {}
+    with mp.get_context("spawn").Pool(4) as pool:
+        for i, fam, n, nnz in pool.imap_unordered(_pool_worker, sorted(tasks, key=lambda t: -t[2])):
+            info[i] = (fam, n, nnz)
+    t_prep = time.perf_counter() - t0
+    torch.cuda.set_device(0)
+    mats = []
+    for i in range(len(tasks)):
+        mats.append(arrow.ArrowMatrix.load(os.path.join(tmp, f"p{i}.arw")))
+        os.remove(os.path.join(tmp, f"p{i}.arw"))
+    os.rmdir(tmp)
+    gen = torch.Generator(device="cuda").manual_seed(12)
+    xin = [torch.randn(m.n * 128, device="cuda", generator=gen).bfloat16() for m in mats]
+    yout = [torch.empty(m.n * 128, device="cuda", dtype=torch.bfloat16) for m in mats]
+    rng = np.random.default_rng(13)
+    count = a.count or 5000
+
+    def make_requests(cnt):
+        return [(int(rng.integers(0, len(mats))), int(rng.choice([16, 32, 64, 128])), int(rng.integers(5, 51)))
+                for _ in range(cnt)]
+
+    budget = 64 << 30
+
+    def run(reqs, arrivals):
+        srv = arrow.ArrowServer(hbm_budget=budget, max_active=64, x_dtype="bf16", max_inflight=2)
+        lat, delay, done_at = {}, {}, {}
+        t_start = time.perf_counter()
+        i = 0
+        n = len(reqs)
+        while len(lat) < n:
+            now = time.perf_counter() - t_start
+            while i < n and arrivals[i] <= now:
+                m, k, it = reqs[i]
+                X = xin[m][: mats[m].n * k].view(mats[m].n, k)
+                Y = yout[m][: mats[m].n * k].view(mats[m].n, k)
+                rid = srv.submit(mats[m], X, Y, it)
+                delay[rid] = (time.perf_counter() - t_start) - arrivals[i]
+                i += 1
+            active = srv.step()
+            for rid, l in srv.poll():
+                lat[rid] = l + delay[rid]
+                done_at[rid] = time.perf_counter() - t_start
+            if active == 0 and i < n and not srv.stats()["inflight_steps"]:
+                time.sleep(max(0.0, min(0.001, arrivals[i] - (time.perf_counter() - t_start))))
+        st = srv.stats()
+        srv.close()
+        span = max(done_at.values()) - min(arrivals)
+        v = np.array(list(lat.values()))
+        return {"requests": n, "throughput_rps": n / span, "p50_ms": float(np.percentile(v, 50) * 1e3),
+                "p99_ms": float(np.percentile(v, 99) * 1e3), "mean_ms": float(v.mean() * 1e3),
+                "steps": st["steps"], "peak_state_bytes": st["peak_bytes"]}
+
+    warm = make_requests(64)
+    run(warm, np.zeros(len(warm)))
+    closed = make_requests(min(count, 2000))
+    cap = run(closed, np.zeros(len(closed)))
+    C = cap["throughput_rps"]
+    results = []
+    for frac in (0.5, 0.8, 0.95):
+        reqs = make_requests(count)
+        arrivals = np.cumsum(rng.exponential(1.0 / (frac * C), count))
+        arrivals -= arrivals[0]
+        r = run(reqs, arrivals)
+        r["rate_rps"] = frac * C
+        r["load"] = frac
+        results.append(r)
+    main = results[1]
+    out = {"metric": "arrow-SpMM serving p50/p99 latency and throughput (continuous batching)",
+           "value": main["throughput_rps"], "unit": "requests/s", "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+           "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": f"{count} requests per rate, Poisson arrivals, pool of {len(mats)} pre-decomposed "
+                                  "matrices (grid / random-geometric / R-MAT, n log-uniform [1e4, 8e6], b = ceil(sqrt n)), "
+                                  "k in {16,32,64,128} BF16, iterations U{5..50}, 64 slots, 64 GiB state budget",
+                      "pool": [{"family": info[i][0], "n": info[i][1], "nnz": info[i][2]} for i in range(len(mats))],
+                      "prep_s": t_prep},
+           "closed_loop": cap, "by_rate": results}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.workload == "batch":
         run_batch(a)
+        return
+    if a.workload == "serve":
+        run_serve(a)
         return
     spec = workload_spec(a)
     if a.impl == "reference":

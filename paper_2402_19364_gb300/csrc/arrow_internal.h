@@ -15,10 +15,10 @@ void set_error(const std::string& msg);
 // Row tiles of the fused row program: at most kTileRows rows and kTileNnz entries each.
 // A tile's row pointers and entries are staged into shared memory with bulk copies.
 #ifndef ARROW_TILE_NNZ
-#define ARROW_TILE_NNZ 2048
+#define ARROW_TILE_NNZ 3072
 #endif
 #ifndef ARROW_TILE_ROWS
-#define ARROW_TILE_ROWS 256
+#define ARROW_TILE_ROWS 384
 #endif
 constexpr int kTileRows = ARROW_TILE_ROWS;
 constexpr int kTileNnz = ARROW_TILE_NNZ;

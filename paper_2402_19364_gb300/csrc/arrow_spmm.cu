@@ -44,7 +44,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 #define ARROW_ROWS_MIN_BLOCKS 3
 #endif
 #ifndef ARROW_ROWS_CARVEOUT
-#define ARROW_ROWS_CARVEOUT 50
+#define ARROW_ROWS_CARVEOUT 75
 #endif
 
 // ------------------------------------------------------------------------------------

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256, 3) arrow_batch_rows_kernel(BatchArgs a) {
 }
 
 #ifndef ARROW_ROWS_CARVEOUT
-#define ARROW_ROWS_CARVEOUT 50
+#define ARROW_ROWS_CARVEOUT 75
 #endif
 // Opt the batched rows kernel into its dynamic shared memory (more than the 48 KB default)
 // and set its carveout; once per instantiation and translation unit.
