@@ -77,8 +77,37 @@ typedef struct {
 /* Fill *o with defaults: seed 0, F32 values, block predicate, upload, all threads. */
 int arrow_opts_default(arrow_opts* o);
 
+/* ---- launch tuning -------------------------------------------------------------------- */
+/* How the fused row program is cut and launched (not in the paper; a property of this GPU
+ * path): rows per tile, entries per tile (>= 1024, so every unsplit row fits), resident CTAs
+ * per SM of the persistent rows kernel (1..3) and the shared-memory carveout in percent.
+ * Defaults: 384, 3072, 3, 75. */
+typedef struct {
+    int32_t tile_rows;
+    int32_t tile_nnz;
+    int32_t ctas_per_sm;
+    int32_t carveout;
+} arrow_tuning;
+
+
 /* ---- handle ------------------------------------------------------------------------ */
 typedef struct arrow_handle_s* arrow_handle;   /* opaque, library-owned */
+
+int arrow_get_tuning(arrow_handle h, arrow_tuning* t);
+
+/* Re-tile the handle (host, O(n)) and, if uploaded, replace its device tile tables; waits for
+ * the device first.  Errors: ARROW_EINVAL (out of range: 32 <= tile_rows <= 2048,
+ * 1024 <= tile_nnz <= 16384, 1 <= ctas_per_sm <= 3, 0 <= carveout <= 100), ARROW_ECUDA. */
+int arrow_set_tuning(arrow_handle h, const arrow_tuning* t);
+
+/* arrow_autotune -- time a fixed set of tunings (tile shapes 128/1024, 256/2048, 384/3072,
+ * 512/4096 rows/entries x 2 or 3 CTAs per SM, carveout fitted to them) with arrow_spmm on the
+ * caller's X, Y (as arrow_spmm) for `iters` iterations each (one warm-up call, two timed),
+ * keep the fastest on the handle, and return it with its milliseconds per call.  Synchronises
+ * `stream`.  Errors: as arrow_spmm and arrow_set_tuning. */
+int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t iters, int32_t x_dtype,
+                   int32_t flags, void* stream, arrow_tuning* best, double* best_ms);
+
 
 /* arrow_decompose -- LA-Decompose(A, b) of Section 4.1 on the host, then (unless
  * opts->flags has ARROW_HOST_ONLY) upload of the decomposition to the device.
@@ -192,6 +221,12 @@ int arrow_batch_create(const arrow_handle* handles, int32_t count, arrow_batch* 
  * the stream when X, Y, k or dtype change.  Errors: ARROW_EINVAL, ARROW_ECUDA. */
 int arrow_batch_spmm(arrow_batch b, const void* const* X, void* const* Y, const int64_t* k, int32_t iters,
                      int32_t x_dtype, int32_t flags, void* stream);
+
+/* arrow_batch_autotune -- arrow_autotune for a whole batch: each candidate tuning is applied to
+ * every handle of the batch, the batch (as arrow_batch_spmm, ARROW_GRAPH) is timed, and the
+ * fastest is kept on all handles.  Synchronises `stream`. */
+int arrow_batch_autotune(arrow_batch b, const void* const* X, void* const* Y, const int64_t* k, int32_t iters,
+                         int32_t x_dtype, void* stream, arrow_tuning* best, double* best_ms);
 
 /* Read and clear the batch's device status word (see arrow_status). */
 int arrow_batch_status(arrow_batch b, int32_t* status);

@@ -192,6 +192,30 @@ class ArrowMatrix:
         _native.check(_native.lib().arrow_profile_get(self._h, int(kernel), ctypes.byref(ms), ctypes.byref(cnt)))
         return float(ms.value), int(cnt.value)
 
+    @property
+    def tuning(self) -> dict:
+        t = _native.ArrowTuning()
+        _native.check(_native.lib().arrow_get_tuning(self._h, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in t._fields_}
+
+    def set_tuning(self, tile_rows: int, tile_nnz: int, ctas_per_sm: int, carveout: int) -> None:
+        t = _native.ArrowTuning(int(tile_rows), int(tile_nnz), int(ctas_per_sm), int(carveout))
+        _native.check(_native.lib().arrow_set_tuning(self._h, ctypes.byref(t)))
+
+    def autotune(self, X, iters: int, *, rescale: bool = False, out=None, stream=None):
+        """``arrow_autotune`` on X: keeps the fastest tuning; returns (tuning dict, ms per call)."""
+        import torch
+        xd = self._check_x(X)
+        if out is None:
+            out = torch.empty_like(X)
+        t = _native.ArrowTuning()
+        ms = ctypes.c_double()
+        _native.check(_native.lib().arrow_autotune(self._h, ctypes.c_void_p(X.data_ptr()),
+                                                   ctypes.c_void_p(out.data_ptr()), X.shape[1], int(iters), xd,
+                                                   ARROW_RESCALE if rescale else 0, _stream_ptr(stream),
+                                                   ctypes.byref(t), ctypes.byref(ms)))
+        return {f: getattr(t, f) for f, _ in t._fields_}, ms.value
+
     def workspace_size(self, k: int, dtype="f32", rescale: bool = False) -> int:
         sz = ctypes.c_size_t()
         _native.check(_native.lib().arrow_workspace_size(self._h, int(k), dtype_code(dtype),
@@ -258,6 +282,21 @@ class ArrowBatch:
         st = ctypes.c_int32()
         _native.check(_native.lib().arrow_batch_status(self._b, ctypes.byref(st)))
         return int(st.value)
+
+    def autotune(self, Xs, iters: int, *, outs=None, stream=None):
+        """``arrow_batch_autotune``: keeps the fastest tuning on every handle; (tuning, ms per call)."""
+        import torch
+        if outs is None:
+            outs = [torch.empty_like(x) for x in Xs]
+        n = len(Xs)
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Xs])
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in outs])
+        ks = (ctypes.c_int64 * n)(*[x.shape[1] for x in Xs])
+        t = _native.ArrowTuning()
+        ms = ctypes.c_double()
+        _native.check(_native.lib().arrow_batch_autotune(self._b, xp, yp, ks, int(iters), dtype_code(Xs[0].dtype),
+                                                         _stream_ptr(stream), ctypes.byref(t), ctypes.byref(ms)))
+        return {f: getattr(t, f) for f, _ in t._fields_}, ms.value
 
     def close(self) -> None:
         if getattr(self, "_b", None) and self._b.value:

@@ -48,6 +48,11 @@ class ArrowStats(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("decompose_seconds", ctypes.c_double)]
 
 
+class ArrowTuning(ctypes.Structure):
+    _fields_ = [("tile_rows", ctypes.c_int32), ("tile_nnz", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("carveout", ctypes.c_int32)]
+
+
 class ArrowServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_int64), ("max_active", ctypes.c_int32), ("x_dtype", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("device", ctypes.c_int32)]
@@ -96,6 +101,12 @@ SIGNATURES = {
     "arrow_profile_get": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "arrow_status": (_I32, [_P, ctypes.POINTER(_I32)]),
     "arrow_selftest_timeout": (_I32, [_I64, ctypes.POINTER(_I32)]),
+    "arrow_get_tuning": (_I32, [_P, ctypes.POINTER(ArrowTuning)]),
+    "arrow_set_tuning": (_I32, [_P, ctypes.POINTER(ArrowTuning)]),
+    "arrow_autotune": (_I32, [_P, _P, _P, _I64, _I32, _I32, _I32, _P, ctypes.POINTER(ArrowTuning),
+                              ctypes.POINTER(ctypes.c_double)]),
+    "arrow_batch_autotune": (_I32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64), _I32, _I32, _P,
+                                    ctypes.POINTER(ArrowTuning), ctypes.POINTER(ctypes.c_double)]),
     "arrow_last_error": (ctypes.c_char_p, []),
 }
 

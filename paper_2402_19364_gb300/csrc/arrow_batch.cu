@@ -60,8 +60,15 @@ void enqueue_typed(arrow_batch_s* B, int iters, cudaStream_t s) {
     const int64_t tot[4] = {B->base[0].back(), B->base[1].back(), B->base[2].back(), B->base[3].back()};
     const int64_t* bases[4] = {db, db + (n_m + 1), db + 2 * (n_m + 1), db + 3 * (n_m + 1)};
     const int sm = B->sm_count;
+    int rows_max = 32, nnz_max = kMinTileNnz, ctas = 3, carve = 75;
+    for (const arrow_handle_s* h : B->hs) {
+        rows_max = std::max(rows_max, h->tune.tile_rows);
+        nnz_max = std::max(nnz_max, h->tune.tile_nnz);
+    }
+    if (!B->hs.empty()) { ctas = B->hs[0]->tune.ctas_per_sm; carve = B->hs[0]->tune.carveout; }
+    const TileLayout L = tile_layout(rows_max, nnz_max);
     auto args = [&](int cls, int parity, int dir) {
-        return BatchArgs{B->d_desc, bases[cls], int32_t(n_m), tot[cls], parity, dir, B->d_status};
+        return BatchArgs{B->d_desc, bases[cls], int32_t(n_m), tot[cls], parity, dir, B->d_status, L.rp, L.col, L.buf};
     };
     auto grid_w = [&](int64_t units, int per_sm) {   // warp-per-unit kernels
         return int(std::max<int64_t>(1, std::min<int64_t>((units + 7) / 8, int64_t(sm) * per_sm)));
@@ -70,8 +77,11 @@ void enqueue_typed(arrow_batch_s* B, int iters, cudaStream_t s) {
     for (int t = 1; t <= iters; ++t) {
         const int parity = (t - 1) & 1;
         if (tot[1]) arrow_batch_segments_kernel<TX, TV><<<grid_w(tot[1], 8), 256, 0, s>>>(args(1, parity, 0));
-        const int rgrid = int(std::max<int64_t>(1, std::min<int64_t>(tot[0], int64_t(sm) * 3)));
-        if (tot[0]) arrow_batch_rows_kernel<TX, TV><<<rgrid, 256, kBatchSmem, s>>>(args(0, parity, 0));
+        const int rgrid = int(std::max<int64_t>(1, std::min<int64_t>(tot[0], int64_t(sm) * ctas)));
+        if (tot[0]) {
+            prepare_batch_rows<TX, TV>(carve);
+            arrow_batch_rows_kernel<TX, TV><<<rgrid, 256, batch_smem_bytes(L), s>>>(args(0, parity, 0));
+        }
         if (tot[2]) arrow_batch_combine_kernel<TX><<<grid_w(tot[2], 4), 256, 0, s>>>(args(2, parity, 0));
     }
     arrow_batch_gather_kernel<TX><<<grid_w(tot[3], 8), 256, 0, s>>>(args(3, iters & 1, 1));
@@ -94,15 +104,20 @@ void enqueue(arrow_batch_s* B, int x_dtype, int iters, cudaStream_t s) {
     }
 }
 
-template <typename TX, typename TV>
-void set_attrs_typed() {
-    prepare_batch_rows<TX, TV>();
-}
 
-void set_attrs(int x_dtype, int v_dtype) {
-    if (x_dtype == ARROW_F32) set_attrs_typed<float, float>();
-    else if (x_dtype == ARROW_BF16) (v_dtype == ARROW_F32) ? set_attrs_typed<__nv_bfloat16, float>() : set_attrs_typed<__nv_bfloat16, __nv_bfloat16>();
-    else (v_dtype == ARROW_F32) ? set_attrs_typed<__half, float>() : set_attrs_typed<__half, __half>();
+// Prefix sums of every kernel class's work units over the batch's matrices, uploaded.
+cudaError_t upload_bases(arrow_batch_s* B) {
+    for (auto& v : B->base) v.assign(1, 0);
+    for (arrow_handle_s* h : B->hs) {
+        const int64_t tiles = h->tile_row.empty() ? 0 : int64_t(h->tile_row.size()) - 1;
+        B->base[0].push_back(B->base[0].back() + tiles);
+        B->base[1].push_back(B->base[1].back() + int64_t(h->seg_begin.size()));
+        B->base[2].push_back(B->base[2].back() + int64_t(h->long_rows.size()));
+        B->base[3].push_back(B->base[3].back() + (h->n + 31) / 32);
+    }
+    std::vector<int64_t> all;
+    for (auto& v : B->base) all.insert(all.end(), v.begin(), v.end());
+    return cudaMemcpy(B->d_base, all.data(), all.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
 }
 
 void batch_release(arrow_batch_s* B) {
@@ -135,18 +150,8 @@ int arrow_batch_create(const arrow_handle* handles, int32_t count, arrow_batch* 
         }
         B->hs.push_back(h);
     }
-    for (auto& v : B->base) v.assign(1, 0);
-    for (arrow_handle_s* h : B->hs) {
-        const int64_t tiles = h->tile_row.empty() ? 0 : int64_t(h->tile_row.size()) - 1;
-        B->base[0].push_back(B->base[0].back() + tiles);
-        B->base[1].push_back(B->base[1].back() + int64_t(h->seg_begin.size()));
-        B->base[2].push_back(B->base[2].back() + int64_t(h->long_rows.size()));
-        B->base[3].push_back(B->base[3].back() + (h->n + 31) / 32);
-    }
-    std::vector<int64_t> all;
-    for (auto& v : B->base) all.insert(all.end(), v.begin(), v.end());
-    cudaError_t e = cudaMalloc(&B->d_base, all.size() * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMemcpy(B->d_base, all.data(), all.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMalloc(&B->d_base, 4 * (B->hs.size() + 1) * sizeof(int64_t));
+    if (e == cudaSuccess) e = upload_bases(B);
     if (e == cudaSuccess) e = cudaMalloc(&B->d_desc, B->hs.size() * sizeof(MatDesc));
     if (e == cudaSuccess) e = cudaMalloc(&B->d_status, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(B->d_status, 0, sizeof(int32_t));
@@ -233,7 +238,6 @@ int arrow_batch_spmm(arrow_batch B, const void* const* X, void* const* Y, const 
         }
         BCK(cudaMemcpy(B->d_desc, B->h_desc.data(), n_m * sizeof(MatDesc), cudaMemcpyHostToDevice));
         B->key = key;
-        set_attrs(x_dtype, B->value_dtype);
     }
     if (!(flags & ARROW_GRAPH)) {
         enqueue(B, x_dtype, iters, s);
@@ -256,6 +260,54 @@ int arrow_batch_spmm(arrow_batch B, const void* const* X, void* const* Y, const 
         B->graph_key = gkey;
     }
     BCK(cudaGraphLaunch(B->exec, s));
+    return ARROW_OK;
+}
+
+int arrow_batch_autotune(arrow_batch B, const void* const* X, void* const* Y, const int64_t* k, int32_t iters,
+                         int32_t x_dtype, void* stream, arrow_tuning* best, double* best_ms) {
+    if (!B || !best || !best_ms || iters <= 0) { set_error("arrow_batch_autotune: bad argument"); return ARROW_EINVAL; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int shapes[4][2] = {{128, 1024}, {256, 2048}, {384, 3072}, {512, 4096}};
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    double bms = 1e30;
+    arrow_tuning bt = B->hs[0]->tune;
+    int rc = ARROW_OK;
+    auto apply = [&](const arrow_tuning& t) {
+        for (arrow_handle_s* h : B->hs)
+            if (int r = arrow_set_tuning(h, &t)) return r;
+        cudaError_t e = upload_bases(B);
+        if (e != cudaSuccess) return cuda_fail(e, "arrow_batch_autotune");
+        B->key.clear();                                    // tile tables moved: rebuild descriptors
+        if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+        return int(ARROW_OK);
+    };
+    for (auto& sh : shapes) {
+        for (int ctas = 2; ctas <= 3; ++ctas) {
+            const TileLayout L = tile_layout(sh[0], sh[1]);
+            const int per = batch_smem_bytes(L) + 1024;
+            const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);
+            arrow_tuning cand{sh[0], sh[1], ctas, pct};
+            if ((rc = apply(cand))) break;
+            if ((rc = arrow_batch_spmm(B, X, Y, k, iters, x_dtype, ARROW_GRAPH, stream))) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 2 && rc == ARROW_OK; ++r) rc = arrow_batch_spmm(B, X, Y, k, iters, x_dtype, ARROW_GRAPH, stream);
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "arrow_batch_autotune"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / 2 < bms) { bms = ms / 2; bt = cand; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if ((rc = apply(bt))) return rc;
+    *best = bt;
+    *best_ms = bms;
     return ARROW_OK;
 }
 

@@ -12,8 +12,9 @@ namespace arrow {
 
 void set_error(const std::string& msg);
 
-// Row tiles of the fused row program: at most kTileRows rows and kTileNnz entries each.
-// A tile's row pointers and entries are staged into shared memory with bulk copies.
+// Row tiles of the fused row program: by default at most kTileRows rows and kTileNnz entries
+// each (arrow_set_tuning / arrow_autotune change them per handle).  A tile's row pointers and
+// entries are staged into shared memory with bulk copies.
 #ifndef ARROW_TILE_NNZ
 #define ARROW_TILE_NNZ 3072
 #endif
@@ -23,6 +24,9 @@ void set_error(const std::string& msg);
 constexpr int kTileRows = ARROW_TILE_ROWS;
 constexpr int kTileNnz = ARROW_TILE_NNZ;
 constexpr int kDefaultLongRow = 64;
+constexpr int kMinTileNnz = 1024;    // split threshold never exceeds this, so every short row fits a tile
+constexpr int kMaxTileRows = 2048;
+constexpr int kMaxTileNnz = 16384;
 constexpr int kDefaultSegment = 512;
 
 // One level i of the decomposition A = sum_i P_{pi_i} B_i P_{pi_i}^T.
@@ -84,6 +88,7 @@ struct arrow_handle_s {
     std::vector<int32_t> long_rows, long_segptr, seg_begin, seg_end;
     std::vector<int32_t> tile_row, tile_ent;
     int32_t long_row = arrow::kDefaultLongRow;
+    arrow_tuning tune{arrow::kTileRows, arrow::kTileNnz, 3, 75};
     double decompose_seconds = 0.0;
     bool uploaded = false;
     arrow::DeviceData dev;
@@ -94,6 +99,8 @@ struct arrow_handle_s {
 namespace arrow {
 // Host decomposition (decompose.cpp).  Fills levels, entry_level and the fused row program.
 int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow_opts& o);
+// (Re)build the row tiles of the fused row program (decompose.cpp).
+void build_tiles(arrow_handle_s* h, int tile_rows, int tile_nnz);
 // Serialisation of the host state (decompose.cpp).
 int save_host(const arrow_handle_s* h, const char* path);
 int load_host(arrow_handle_s* h, const char* path);

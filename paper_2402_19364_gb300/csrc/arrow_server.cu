@@ -136,8 +136,16 @@ size_t footprint(const arrow_handle_s* h, int64_t k, int dt) {
 template <typename TX, typename TV>
 void launch_step(arrow_server_s* S, const int64_t* tot, int n_m, cudaStream_t s) {
     const int64_t* db = S->d_base;
+    int rows_max = 32, nnz_max = kMinTileNnz;
+    for (const Request& r : S->active) {
+        rows_max = std::max(rows_max, r.h->tune.tile_rows);
+        nnz_max = std::max(nnz_max, r.h->tune.tile_nnz);
+    }
+    const TileLayout L = tile_layout(rows_max, nnz_max);
+    const int ctas = S->active.empty() ? 3 : S->active[0].h->tune.ctas_per_sm;
+    const int carve = S->active.empty() ? 75 : S->active[0].h->tune.carveout;
     auto args = [&](int cls, int parity, int dir) {
-        return BatchArgs{S->d_desc, db + cls * (n_m + 1), n_m, tot[cls], parity, dir, S->d_status};
+        return BatchArgs{S->d_desc, db + cls * (n_m + 1), n_m, tot[cls], parity, dir, S->d_status, L.rp, L.col, L.buf};
     };
     const int sm = S->sm_count;
     auto grid_w = [&](int64_t units, int per_sm) {
@@ -146,9 +154,9 @@ void launch_step(arrow_server_s* S, const int64_t* tot, int n_m, cudaStream_t s)
     if (tot[0]) arrow_batch_gather_kernel<TX><<<grid_w(tot[0], 8), 256, 0, s>>>(args(0, 0, 0));
     if (tot[1]) arrow_batch_segments_kernel<TX, TV><<<grid_w(tot[1], 8), 256, 0, s>>>(args(1, 0, 0));
     if (tot[2]) {
-        prepare_batch_rows<TX, TV>();
-        const int g = int(std::max<int64_t>(1, std::min<int64_t>(tot[2], int64_t(sm) * 3)));
-        arrow_batch_rows_kernel<TX, TV><<<g, 256, kBatchSmem, s>>>(args(2, 0, 0));
+        prepare_batch_rows<TX, TV>(carve);
+        const int g = int(std::max<int64_t>(1, std::min<int64_t>(tot[2], int64_t(sm) * ctas)));
+        arrow_batch_rows_kernel<TX, TV><<<g, 256, batch_smem_bytes(L), s>>>(args(2, 0, 0));
     }
     if (tot[3]) arrow_batch_combine_kernel<TX><<<grid_w(tot[3], 4), 256, 0, s>>>(args(3, 0, 0));
     if (tot[4]) arrow_batch_gather_kernel<TX><<<grid_w(tot[4], 8), 256, 0, s>>>(args(4, 1, 1));

@@ -39,20 +39,18 @@ namespace arrow {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
-// CTAs of the rows kernel resident per SM (register cap) and shared-memory carveout (%).
+// CTAs of the rows kernel that fit an SM by registers (launch bound); arrow_tuning's
+// ctas_per_sm stays at or below it.
 #ifndef ARROW_ROWS_MIN_BLOCKS
 #define ARROW_ROWS_MIN_BLOCKS 3
-#endif
-#ifndef ARROW_ROWS_CARVEOUT
-#define ARROW_ROWS_CARVEOUT 75
 #endif
 
 // ------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------
-// + per-warp FP64 column sums of squares (8 warps x kc doubles) after the two buffers
-constexpr int kRowsSmemBase = 128 + kStages * kBufBytes;
-static inline int rows_smem_bytes(int kc) { return kRowsSmemBase + 8 * kc * 8; }
+// dynamic shared memory: pipeline state, kStages tile buffers, per-warp FP64 column sums
+// of squares (8 warps x kc doubles)
+static inline int rows_smem_bytes(const TileLayout& L, int kc) { return 128 + kStages * L.buf + 8 * kc * 8; }
 
 struct RowArgs {
     const int32_t* rowptr;     // short-row stream
@@ -69,13 +67,14 @@ struct RowArgs {
     const double* scale;       // [k] per-column factor d_{t-1}, or null
     double* norm_partials;     // [gridDim.x][k] (rows kernel slots), or null
     int32_t* status;
+    int32_t rp_bytes, col_bytes, buf_bytes;   // shared-memory layout of a staged tile
 };
 
 // Thread 0: stage tile t (row pointers, columns, values) into buf with three bulk copies.
 template <typename TV>
 __device__ __forceinline__ void issue_tile(const RowArgs& a, int t, unsigned char* buf, uint64_t* bar) {
     stage_tile<TV>(a.rowptr, a.col, static_cast<const TV*>(a.val), a.tile_row[t], a.tile_row[t + 1], a.tile_ent[t],
-                   a.tile_ent[t + 1], buf, bar);
+                   a.tile_ent[t + 1], buf, bar, a.rp_bytes, a.col_bytes);
 }
 
 // Fused arrow-row kernel (persistent).  Each CTA walks row tiles t = blockIdx.x, +gridDim.x,
@@ -95,7 +94,7 @@ __global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(
     extern __shared__ __align__(128) unsigned char smem[];
     PipeSmem* ps = reinterpret_cast<PipeSmem*>(smem);
     unsigned char* bufs = smem + 128;
-    double* wsum = reinterpret_cast<double*>(smem + kRowsSmemBase);   // [8][kc]
+    double* wsum = reinterpret_cast<double*>(smem + 128 + kStages * a.buf_bytes);   // [8][kc]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int tl = threadIdx.x & (T - 1);
@@ -120,7 +119,7 @@ __global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(
     if (threadIdx.x == 0)
         for (int b = 0; b < kStages; ++b)
             if (int(blockIdx.x) + b * G < a.n_tiles) {
-                issue_tile<TV>(a, blockIdx.x + b * G, bufs + b * kBufBytes, &ps->full[b]);
+                issue_tile<TV>(a, blockIdx.x + b * G, bufs + b * a.buf_bytes, &ps->full[b]);
                 ps->issued[b]++;
             }
     float scl[V];
@@ -133,7 +132,7 @@ __global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(
     int i = 0;
     for (int t = blockIdx.x; t < a.n_tiles; t += G, ++i) {
         const int b = i % kStages;
-        unsigned char* buf = bufs + b * kBufBytes;
+        unsigned char* buf = bufs + b * a.buf_bytes;
         const bool ok = mbar_wait_bounded(&ps->full[b], (i / kStages) & 1, kWaitLimitNs);
         if (__any_sync(0xffffffffu, !ok)) {
             if (lane == 0) { ps->failed = 1; atomicExch(a.status, kStatusTimeout); }
@@ -141,8 +140,8 @@ __global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(
         }
         const int r0 = __ldg(a.tile_row + t), r1 = __ldg(a.tile_row + t + 1), e0 = __ldg(a.tile_ent + t);
         const int32_t* srp = reinterpret_cast<const int32_t*>(buf) + (r0 & 3);
-        const int32_t* scol = reinterpret_cast<const int32_t*>(buf + kRpBytes) + (e0 & 3);
-        const TV* sval = reinterpret_cast<const TV*>(buf + kRpBytes + kColBytes) + (e0 & (VE - 1));
+        const int32_t* scol = reinterpret_cast<const int32_t*>(buf + a.rp_bytes) + (e0 & 3);
+        const TV* sval = reinterpret_cast<const TV*>(buf + a.rp_bytes + a.col_bytes) + (e0 & (VE - 1));
         const int nrows = r1 - r0;
         for (int j = team; j < nrows; j += TEAMS) {
             const int s = srp[j] - e0, e = srp[j + 1] - e0;
@@ -195,7 +194,7 @@ __global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(
             release_buffer(ps, b, NW, [&](int bb) {
                 const int tn = t + kStages * G;
                 if (tn < a.n_tiles) {
-                    issue_tile<TV>(a, tn, bufs + bb * kBufBytes, &ps->full[bb]);
+                    issue_tile<TV>(a, tn, bufs + bb * a.buf_bytes, &ps->full[bb]);
                     ps->issued[bb]++;
                 }
             });
@@ -397,13 +396,16 @@ __global__ void __launch_bounds__(256) arrow_gather_rows_kernel(const TX* __rest
                                                                 const double* __restrict__ scale) {
     using P = Pack<TX>;
     constexpr int V = P::V;
-    constexpr int U = 4;
+    constexpr int U = 8;
     const int nv = int(k / V);
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     if (nv <= 32) {
         const int rpw = 32 / nv, lr = lane / nv, lq = lane - lr * nv;
+        float sc[V];   // the column factors of this lane, rounded once to FP32
+#pragma unroll
+        for (int v = 0; v < V; ++v) sc[v] = scale ? float(scale[lq * V + v]) : 1.0f;
         for (int64_t g = warp; g * rpw < n; g += nwarps * U) {
             uint4 u[U];
 #pragma unroll
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(256) arrow_gather_rows_kernel(const TX* __rest
                         float f[V];
                         P::to_float(o, f);
 #pragma unroll
-                        for (int v = 0; v < V; ++v) f[v] = float(double(f[v]) * scale[lq * V + v]);
+                        for (int v = 0; v < V; ++v) f[v] *= sc[v];
                         o = P::from_float(f);
                     }
                     *reinterpret_cast<uint4*>(dst + r * k + lq * V) = o;
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(256) arrow_gather_rows_kernel(const TX* __rest
                     float f[V];
                     P::to_float(o, f);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) f[v] = float(double(f[v]) * scale[q * V + v]);
+                    for (int v = 0; v < V; ++v) f[v] *= float(scale[q * V + v]);
                     o = P::from_float(f);
                 }
                 *reinterpret_cast<uint4*>(dst + r * k + q * V) = o;
@@ -616,22 +618,22 @@ struct Plan {
     size_t x_bytes, part_bytes, np_bytes, sc_bytes, total;
 };
 
-template <typename TX, typename TV, int T, bool R>
-static int rows_blocks_per_sm() {
-    static int cached = 0;
-    if (!cached) {
-        constexpr int kc = T * Pack<TX>::V;
-        cudaFuncSetAttribute(arrow_rows_kernel<TX, TV, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             rows_smem_bytes(kc));
-        cudaFuncSetAttribute(arrow_rows_kernel<TX, TV, T, R>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             ARROW_ROWS_CARVEOUT);
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, arrow_rows_kernel<TX, TV, T, R>, 256,
-                                                          rows_smem_bytes(kc)) != cudaSuccess || nb < 1)
-            nb = 1;
-        cached = nb;
-    }
-    return cached;
+// Shared-memory opt-in (once per function) and carveout (when it changes) of a kernel.
+static void set_smem_attrs(const void* fn, int carveout) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, int>> seen;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& e : seen)
+        if (e.first == fn) {
+            if (e.second != carveout) {
+                cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+                e.second = carveout;
+            }
+            return;
+        }
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+    seen.emplace_back(fn, carveout);
 }
 
 static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags, Plan& p) {
@@ -647,9 +649,9 @@ static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags,
     }
     p.kc = p.T * p.V;
     const int sm = h->dev.sm_count > 0 ? h->dev.sm_count : 1;
-    // persistent rows kernel: up to 4 CTAs per SM (the occupancy bound is applied at launch)
+    // persistent rows kernel: ctas_per_sm CTAs per SM (one FP64 norm slot each)
     const int64_t n_tiles = h->tile_row.empty() ? 0 : int64_t(h->tile_row.size()) - 1;
-    p.rows_grid = int(std::max<int64_t>(1, std::min<int64_t>(n_tiles, int64_t(sm) * ARROW_ROWS_MIN_BLOCKS)));
+    p.rows_grid = int(std::max<int64_t>(1, std::min<int64_t>(n_tiles, int64_t(sm) * h->tune.ctas_per_sm)));
     const int64_t n_long = int64_t(h->long_rows.size());
     const int64_t teams = 256 / p.T;
     p.comb_grid = n_long ? int(std::max<int64_t>(1, std::min<int64_t>((n_long + teams - 1) / teams, int64_t(sm) * 2))) : 0;
@@ -677,16 +679,17 @@ static void launch_step(const arrow_handle_s* h, const Plan& p, const TX* cur, T
             arrow_segments_kernel<TX, TV, T><<<grid, 256, 0, s>>>(sa);
             pf.end(ARROW_K_SEGMENTS, e0);
         }
-        RowArgs ra{d.rowptr, d.col, d.val, d.tile_row, d.tile_ent, n_tiles, cur, nxt, k, koff, p.kc, scale_in, np, d.status};
+        const TileLayout L = tile_layout(h->tune.tile_rows, h->tune.tile_nnz);
+        RowArgs ra{d.rowptr, d.col, d.val, d.tile_row, d.tile_ent, n_tiles, cur, nxt, k, koff, p.kc, scale_in, np,
+                   d.status, L.rp, L.col, L.buf};
+        const int smem = rows_smem_bytes(L, p.kc);
         cudaEvent_t e0 = pf.begin();
         if (np) {
-            const int grid = std::min(p.rows_grid, d.sm_count * rows_blocks_per_sm<TX, TV, T, true>());
-            // the norm partial slots are indexed by blockIdx.x: unused slots must hold zero
-            if (grid < p.rows_grid) cudaMemsetAsync(np, 0, size_t(p.rows_grid) * size_t(k) * 8, s);
-            arrow_rows_kernel<TX, TV, T, true><<<grid, 256, rows_smem_bytes(p.kc), s>>>(ra);
+            set_smem_attrs(reinterpret_cast<const void*>(arrow_rows_kernel<TX, TV, T, true>), h->tune.carveout);
+            arrow_rows_kernel<TX, TV, T, true><<<p.rows_grid, 256, smem, s>>>(ra);
         } else {
-            const int grid = std::min(p.rows_grid, d.sm_count * rows_blocks_per_sm<TX, TV, T, false>());
-            arrow_rows_kernel<TX, TV, T, false><<<grid, 256, rows_smem_bytes(p.kc), s>>>(ra);
+            set_smem_attrs(reinterpret_cast<const void*>(arrow_rows_kernel<TX, TV, T, false>), h->tune.carveout);
+            arrow_rows_kernel<TX, TV, T, false><<<p.rows_grid, 256, smem, s>>>(ra);
         }
         pf.end(ARROW_K_ROWS, e0);
         if (p.comb_grid) {
@@ -740,7 +743,7 @@ static int spmm_typed(const arrow_handle_s* h, const Plan& p, const void* X, int
     double* sc = reinterpret_cast<double*>(ws + 2 * p.x_bytes + p.part_bytes + p.np_bytes);
     const int64_t n = h->n;
     const int64_t vecs = n * (k / p.V);
-    const int ggrid = int(std::max<int64_t>(1, std::min<int64_t>((vecs + 1023) / 1024, int64_t(d.sm_count) * 8)));
+    const int ggrid = int(std::max<int64_t>(1, std::min<int64_t>((vecs + 2047) / 2048, int64_t(d.sm_count) * 8)));
     cudaEvent_t e0 = pf.begin();
     arrow_gather_rows_kernel<TX><<<ggrid, 256, 0, s>>>(static_cast<const TX*>(X), xa, d.iperm0, n, k, nullptr);
     pf.end(ARROW_K_PERMUTE, e0);
@@ -942,7 +945,7 @@ int arrow_handle_copy(arrow_handle h, int32_t value_dtype, arrow_handle* out) {
         c->levels = h->levels;
         c->f_rowptr = h->f_rowptr; c->f_col = h->f_col; c->f_src = h->f_src; c->l_col = h->l_col; c->l_src = h->l_src;
         c->long_rows = h->long_rows; c->long_segptr = h->long_segptr; c->seg_begin = h->seg_begin; c->seg_end = h->seg_end;
-        c->tile_row = h->tile_row; c->tile_ent = h->tile_ent; c->long_row = h->long_row;
+        c->tile_row = h->tile_row; c->tile_ent = h->tile_ent; c->long_row = h->long_row; c->tune = h->tune;
         c->decompose_seconds = h->decompose_seconds;
     } catch (const std::bad_alloc&) {
         delete c;
@@ -1042,6 +1045,81 @@ int arrow_spmm_static(arrow_handle h, const void* X, int64_t k, int32_t iters, v
     // leaves unwritten are cleared by the launch code before each step.
     return spmm_dispatch(h, p, X, k, iters, Y, x_dtype, flags, static_cast<char*>(scratch),
                          static_cast<cudaStream_t>(stream));
+}
+
+int arrow_get_tuning(arrow_handle h, arrow_tuning* t) {
+    if (!h || !t) { set_error("arrow_get_tuning: NULL argument"); return ARROW_EINVAL; }
+    *t = h->tune;
+    return ARROW_OK;
+}
+
+int arrow_set_tuning(arrow_handle h, const arrow_tuning* t) {
+    if (!h || !t) { set_error("arrow_set_tuning: NULL argument"); return ARROW_EINVAL; }
+    if (t->tile_rows < 32 || t->tile_rows > kMaxTileRows || t->tile_nnz < kMinTileNnz || t->tile_nnz > kMaxTileNnz ||
+        t->ctas_per_sm < 1 || t->ctas_per_sm > 3 || t->carveout < 0 || t->carveout > 100) {
+        set_error("arrow_set_tuning: value out of range");
+        return ARROW_EINVAL;
+    }
+    if (rows_smem_bytes(tile_layout(t->tile_rows, t->tile_nnz), 256) > 227 * 1024) {
+        set_error("arrow_set_tuning: tile too large for shared memory");
+        return ARROW_EINVAL;
+    }
+    if (h->opts.predicate != ARROW_PRED_BLOCK) { set_error("arrow_set_tuning: band-predicate handles have no device path"); return ARROW_EINVAL; }
+    const bool retile = t->tile_rows != h->tune.tile_rows || t->tile_nnz != h->tune.tile_nnz;
+    if (retile) {
+        build_tiles(h, t->tile_rows, t->tile_nnz);
+        if (h->uploaded) {
+            ACK(cudaDeviceSynchronize());
+            if (h->dev.tile_row) cudaFree(h->dev.tile_row);
+            if (h->dev.tile_ent) cudaFree(h->dev.tile_ent);
+            h->dev.tile_row = h->dev.tile_ent = nullptr;
+            size_t bytes = 0;
+            int rc;
+            if ((rc = upload_vec(&h->dev.tile_row, h->tile_row, bytes))) return rc;
+            if ((rc = upload_vec(&h->dev.tile_ent, h->tile_ent, bytes))) return rc;
+        }
+    }
+    h->tune = *t;
+    return ARROW_OK;
+}
+
+int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t iters, int32_t x_dtype, int32_t flags,
+                   void* stream, arrow_tuning* best, double* best_ms) {
+    if (!h || !best || !best_ms || iters <= 0) { set_error("arrow_autotune: bad argument"); return ARROW_EINVAL; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int shapes[4][2] = {{128, 1024}, {256, 2048}, {384, 3072}, {512, 4096}};
+    cudaEvent_t e0, e1;
+    ACK(cudaEventCreate(&e0));
+    ACK(cudaEventCreate(&e1));
+    double bms = 1e30;
+    arrow_tuning bt = h->tune;
+    int rc = ARROW_OK;
+    for (auto& sh : shapes) {
+        for (int ctas = 2; ctas <= 3 && rc == ARROW_OK; ++ctas) {
+            const TileLayout L = tile_layout(sh[0], sh[1]);
+            const int per = rows_smem_bytes(L, 128) + 1024;
+            const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);
+            arrow_tuning cand{sh[0], sh[1], ctas, pct};
+            if ((rc = arrow_set_tuning(h, &cand))) break;
+            if ((rc = arrow_spmm(h, X, k, iters, Y, x_dtype, flags, stream))) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 2 && rc == ARROW_OK; ++r) rc = arrow_spmm(h, X, k, iters, Y, x_dtype, flags, stream);
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "arrow_autotune"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / 2 < bms) { bms = ms / 2; bt = cand; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if ((rc = arrow_set_tuning(h, &bt))) return rc;
+    *best = bt;
+    *best_ms = bms;
+    return ARROW_OK;
 }
 
 int arrow_num_levels(arrow_handle h, int32_t* l) {

@@ -41,6 +41,7 @@ struct BatchArgs {
     int32_t parity;        // 0: xa -> xb, 1: xb -> xa
     int32_t dir;           // gather: 0 permute-in, 1 permute-out
     int32_t* status;
+    int32_t rp_bytes, col_bytes, buf_bytes;   // staged-tile layout (rows kernel)
 };
 
 __device__ __forceinline__ int find_mat(const int64_t* base, int n, int64_t w) {
@@ -52,7 +53,7 @@ __device__ __forceinline__ int find_mat(const int64_t* base, int n, int64_t w) {
     return lo;
 }
 
-constexpr int kBatchSmem = 128 + kStages * kBufBytes;
+inline int batch_smem_bytes(const TileLayout& L) { return 128 + kStages * L.buf; }
 
 // Rows of every matrix's tiles (the fused arrow-row kernel of arrow_spmm with a per-tile
 // matrix descriptor and a run-time team width); same tile pipeline without block barriers.
@@ -73,7 +74,8 @@ __global__ void __launch_bounds__(256, 3) arrow_batch_rows_kernel(BatchArgs a) {
         const int t = int(w - a.base[m]);
         const int r0 = d.tile_row[t], r1 = d.tile_row[t + 1], e0 = d.tile_ent[t], e1 = d.tile_ent[t + 1];
         ps->hdr[b][0] = m; ps->hdr[b][1] = r0; ps->hdr[b][2] = r1; ps->hdr[b][3] = e0;
-        stage_tile<TV>(d.rowptr, d.col, static_cast<const TV*>(d.val), r0, r1, e0, e1, bufs + b * kBufBytes, &ps->full[b]);
+        stage_tile<TV>(d.rowptr, d.col, static_cast<const TV*>(d.val), r0, r1, e0, e1, bufs + b * a.buf_bytes, &ps->full[b],
+                       a.rp_bytes, a.col_bytes);
         ps->issued[b]++;
     };
     if (threadIdx.x == 0) {
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(256, 3) arrow_batch_rows_kernel(BatchArgs a) {
     int i = 0;
     for (int64_t w = blockIdx.x; w < a.total; w += G, ++i) {
         const int b = i % kStages;
-        unsigned char* buf = bufs + b * kBufBytes;
+        unsigned char* buf = bufs + b * a.buf_bytes;
         const bool ok = mbar_wait_bounded(&ps->full[b], (i / kStages) & 1, kWaitLimitNs);
         if (__any_sync(0xffffffffu, !ok)) {
             if (lane == 0) { ps->failed = 1; atomicExch(a.status, kStatusTimeout); }
@@ -108,8 +110,8 @@ __global__ void __launch_bounds__(256, 3) arrow_batch_rows_kernel(BatchArgs a) {
         const TX* __restrict__ X = static_cast<const TX*>(par ? d.xb : d.xa) + tl * V;
         TX* __restrict__ Y = static_cast<TX*>(par ? d.xa : d.xb) + tl * V;
         const int32_t* srp = reinterpret_cast<const int32_t*>(buf) + (r0 & 3);
-        const int32_t* scol = reinterpret_cast<const int32_t*>(buf + kRpBytes) + (e0 & 3);
-        const TV* sval = reinterpret_cast<const TV*>(buf + kRpBytes + kColBytes) + (e0 & (VE - 1));
+        const int32_t* scol = reinterpret_cast<const int32_t*>(buf + a.rp_bytes) + (e0 & 3);
+        const TV* sval = reinterpret_cast<const TV*>(buf + a.rp_bytes + a.col_bytes) + (e0 & (VE - 1));
         const int nrows = r1 - r0;
         for (int j = team; j < nrows; j += teams) {
             const int s = srp[j] - e0, e = srp[j + 1] - e0;
@@ -146,19 +148,16 @@ __global__ void __launch_bounds__(256, 3) arrow_batch_rows_kernel(BatchArgs a) {
     if (ps->failed && threadIdx.x == 0) drain_pipeline(ps);
 }
 
-#ifndef ARROW_ROWS_CARVEOUT
-#define ARROW_ROWS_CARVEOUT 75
-#endif
-// Opt the batched rows kernel into its dynamic shared memory (more than the 48 KB default)
-// and set its carveout; once per instantiation and translation unit.
+// Opt the batched rows kernel into large dynamic shared memory (once) and set its carveout
+// (when it changes); per instantiation and translation unit.
 template <typename TX, typename TV>
-inline void prepare_batch_rows() {
-    static bool done = false;
-    if (done) return;
-    cudaFuncSetAttribute(arrow_batch_rows_kernel<TX, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
-    cudaFuncSetAttribute(arrow_batch_rows_kernel<TX, TV>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         ARROW_ROWS_CARVEOUT);
-    done = true;
+inline void prepare_batch_rows(int carveout) {
+    static int last = -1;
+    if (last == carveout) return;
+    if (last < 0)
+        cudaFuncSetAttribute(arrow_batch_rows_kernel<TX, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(arrow_batch_rows_kernel<TX, TV>, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+    last = carveout;
 }
 
 // One warp per split-row segment of any matrix (first stage of the head-row reduction).

@@ -424,6 +424,29 @@ void arrange(int64_t n, const std::vector<int32_t>& head, const std::vector<uint
 
 }  // namespace
 
+void build_tiles(arrow_handle_s* h, int tile_rows, int tile_nnz) {
+    // consecutive rows, at most tile_rows rows and tile_nnz entries (short rows only)
+    const int64_t n = h->n;
+    h->tile_row.assign(1, 0);
+    h->tile_ent.assign(1, 0);
+    if (h->f_rowptr.empty()) return;
+    int64_t r = 0;
+    while (r < n) {
+        int64_t r1 = r, ent = 0;
+        while (r1 < n && r1 - r < tile_rows) {
+            int64_t l = h->f_rowptr[r1 + 1] - h->f_rowptr[r1];
+            if (ent + l > tile_nnz) break;
+            ent += l;
+            ++r1;
+        }
+        h->tile_row.push_back(int32_t(r1));
+        h->tile_ent.push_back(h->f_rowptr[r1]);
+        r = r1;
+    }
+    h->tune.tile_rows = tile_rows;
+    h->tune.tile_nnz = tile_nnz;
+}
+
 int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow_opts& o) {
     auto t0 = std::chrono::steady_clock::now();
     g_threads = o.nthreads > 0 ? o.nthreads : int(std::max(1u, std::thread::hardware_concurrency()));
@@ -552,7 +575,7 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
         const int32_t* perm0 = nl ? h->levels[0].perm.data() : nullptr;
         if (nl) for (int64_t v = 0; v < n; ++v) iperm0[perm0[v]] = int32_t(v);
         else std::iota(iperm0.begin(), iperm0.end(), 0);
-        const int32_t long_row = std::min(o.long_row > 0 ? o.long_row : kDefaultLongRow, kTileNnz);
+        const int32_t long_row = std::min(o.long_row > 0 ? o.long_row : kDefaultLongRow, kMinTileNnz);
         const int32_t seg = o.segment > 0 ? o.segment : kDefaultSegment;
         h->long_row = long_row;
         std::vector<int32_t> len(n);
@@ -607,22 +630,7 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
                 }
             }
         });
-        // row tiles: consecutive rows, at most kTileRows rows and kTileNnz entries
-        h->tile_row.assign(1, 0);
-        h->tile_ent.assign(1, 0);
-        int64_t r = 0;
-        while (r < n) {
-            int64_t r1 = r, ent = 0;
-            while (r1 < n && r1 - r < kTileRows) {
-                int64_t l = h->f_rowptr[r1 + 1] - h->f_rowptr[r1];
-                if (ent + l > kTileNnz) break;
-                ent += l;
-                ++r1;
-            }
-            h->tile_row.push_back(int32_t(r1));
-            h->tile_ent.push_back(h->f_rowptr[r1]);
-            r = r1;
-        }
+        build_tiles(h, h->tune.tile_rows, h->tune.tile_nnz);
     }
     h->decompose_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return ARROW_OK;
@@ -641,7 +649,7 @@ namespace arrow {
 namespace {
 
 constexpr char kMagic[8] = {'A', 'R', 'W', 'D', 'E', 'C', '1', '\0'};
-constexpr int64_t kVersion = 1;
+constexpr int64_t kVersion = 2;
 
 struct Writer {
     FILE* f;
@@ -689,6 +697,7 @@ int save_host(const arrow_handle_s* h, const char* path) {
     w.val(h->n); w.val(h->nnz); w.val(h->b);
     w.val(h->opts);
     w.val(h->long_row);
+    w.val(h->tune);
     w.val(h->decompose_seconds);
     w.val(int64_t(h->levels.size()));
     for (const Level& l : h->levels) {
@@ -723,6 +732,7 @@ int load_host(arrow_handle_s* h, const char* path) {
     r.val(h->n); r.val(h->nnz); r.val(h->b);
     r.val(h->opts);
     r.val(h->long_row);
+    r.val(h->tune);
     r.val(h->decompose_seconds);
     r.val(nl);
     const int64_t n = h->n, nnz = h->nnz;

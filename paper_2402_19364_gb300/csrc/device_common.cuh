@@ -141,13 +141,6 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Shared-memory layout of one staged tile: row pointers, column indices, values, each a
-// 16-byte aligned superset of the tile's range.
-constexpr int kRpBytes = ((kTileRows + 1 + 6) * 4 + 15) / 16 * 16;
-constexpr int kColBytes = ((kTileNnz + 8) * 4 + 15) / 16 * 16;
-constexpr int kValBytes = kColBytes;
-constexpr int kBufBytes = (kRpBytes + kColBytes + kValBytes + 127) / 128 * 128;
-
 // Tile pipeline state at the start of dynamic shared memory (128 bytes): one "full"
 // mbarrier per staging buffer (completed by the buffer's bulk copies), the number of warps
 // done with the buffer's current use, the buffer's issued uses, and a small header.
@@ -185,11 +178,25 @@ __device__ __forceinline__ void drain_pipeline(PipeSmem* ps) {
         if (ps->issued[b] > 0) mbar_wait_bounded(&ps->full[b], uint32_t((ps->issued[b] - 1) & 1), kWaitLimitNs);
 }
 
+// Shared-memory layout of one staged tile of at most tile_rows rows and tile_nnz entries: row
+// pointers, column indices and values, each a 16-byte aligned superset of the tile's range.
+struct TileLayout {
+    int rp, col, buf;   // bytes of the row-pointer and column regions, bytes of one whole buffer
+};
+__host__ __device__ inline TileLayout tile_layout(int tile_rows, int tile_nnz) {
+    TileLayout L;
+    L.rp = ((tile_rows + 1 + 6) * 4 + 15) / 16 * 16;
+    L.col = ((tile_nnz + 8) * 4 + 15) / 16 * 16;
+    L.buf = (L.rp + 2 * L.col + 127) / 128 * 128;   // values take at most as much as columns
+    return L;
+}
+
 // Stage the row tile [r0, r1) with entries [e0, e1) into buf: row pointers, columns and values,
 // each as a 16-byte aligned superset (the arrays are padded by 64 bytes), completing on bar.
 template <typename TV>
 __device__ __forceinline__ void stage_tile(const int32_t* rowptr, const int32_t* col, const TV* val, int r0, int r1,
-                                           int e0, int e1, unsigned char* buf, uint64_t* bar) {
+                                           int e0, int e1, unsigned char* buf, uint64_t* bar, int rp_bytes,
+                                           int col_bytes) {
     constexpr int VE = 16 / int(sizeof(TV));
     const int ra = r0 & ~3, rb = (r1 + 1 + 3) & ~3;
     const int ca = e0 & ~3, cb = (e1 + 3) & ~3;
@@ -199,8 +206,8 @@ __device__ __forceinline__ void stage_tile(const int32_t* rowptr, const int32_t*
     const uint32_t bval = uint32_t(vb - va) * uint32_t(sizeof(TV));
     mbar_arrive_expect_tx(bar, brp + bcol + bval);
     bulk_g2s(buf, rowptr + ra, brp, bar);
-    if (bcol) bulk_g2s(buf + kRpBytes, col + ca, bcol, bar);
-    if (bval) bulk_g2s(buf + kRpBytes + kColBytes, val + va, bval, bar);
+    if (bcol) bulk_g2s(buf + rp_bytes, col + ca, bcol, bar);
+    if (bval) bulk_g2s(buf + rp_bytes + col_bytes, val + va, bval, bar);
 }
 
 }  // namespace arrow

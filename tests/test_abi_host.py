@@ -180,3 +180,18 @@ def test_save_load_roundtrip_and_corruption(arrow, tmp_path):
         arrow.ArrowMatrix.load(short, host_only=True)
     with pytest.raises(arrow.ArrowError):
         arrow.ArrowMatrix.load(tmp_path / "missing.arw", host_only=True)
+
+
+def test_tuning_retiles_and_validates(arrow):
+    A = w.grid3d(30)
+    M = arrow.ArrowMatrix(A, 256, host_only=True)
+    t = M.tuning
+    assert (t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"]) == (384, 3072, 3, 75)
+    n_default = M.stats()["tiles"]
+    M.set_tuning(128, 1024, 2, 50)
+    assert M.tuning["tile_rows"] == 128 and M.stats()["tiles"] > n_default
+    assert M.stats()["tiles"] >= (A.n + 127) // 128
+    for bad in ((16, 1024, 2, 50), (128, 512, 2, 50), (128, 1024, 4, 50), (128, 1024, 2, 101), (4096, 1024, 2, 50)):
+        with pytest.raises(arrow.ArrowError):
+            M.set_tuning(*bad)
+    assert M.tuning["tile_rows"] == 128                      # unchanged after rejected values

@@ -101,3 +101,33 @@ def test_handle_copy_same_structure(arrow):
     Yf = M.spmm(X, 3)
     Yh = C.spmm(X.half(), 3).float()
     assert torch.linalg.vector_norm(Yh - Yf) / torch.linalg.vector_norm(Yf) < 2e-2
+
+
+def test_tunings_give_same_bits_and_autotune_keeps_one(arrow):
+    # the row arithmetic does not depend on the tiling; the FP64 norm sums are grouped by
+    # CTA, so with the rescale the results agree within the FP32 tolerance instead
+    A = w.grid3d(40, seed=5)
+    M = arrow.ArrowMatrix(A, 512)
+    X = torch.from_numpy(w.features(A.n, 16, seed=2)).cuda()
+    ref = M.spmm(X, 5)
+    ref_r = M.spmm(X, 5, rescale=True)
+    for tr, tn, c, co in ((128, 1024, 2, 40), (512, 4096, 3, 100), (256, 2048, 1, 30)):
+        M.set_tuning(tr, tn, c, co)
+        assert torch.equal(M.spmm(X, 5), ref)
+        Yr = M.spmm(X, 5, rescale=True)
+        assert float(((Yr - ref_r).abs().max(0).values / ref_r.abs().max(0).values).max()) <= 5e-5
+    best, ms = M.autotune(X, 5, rescale=True)
+    assert ms > 0 and best == M.tuning
+    assert torch.equal(M.spmm(X, 5), ref)
+
+
+def test_batch_autotune(arrow):
+    mats, ks = _rgg_batch(6, 3)
+    ms = [arrow.ArrowMatrix(A, int(np.ceil(np.sqrt(A.n))), value_dtype="f16") for A in mats]
+    Xs = [torch.from_numpy(w.features(A.n, k, seed=i)).to("cuda", torch.float16) for i, (A, k) in enumerate(zip(mats, ks))]
+    B = arrow.ArrowBatch(ms)
+    ref = [y.clone() for y in B.spmm(Xs, 4, graph=True)]
+    best, t = B.autotune(Xs, 4)
+    assert t > 0 and all(m.tuning == best for m in ms)
+    for y, r in zip(B.spmm(Xs, 4, graph=True), ref):
+        assert torch.equal(y, r)

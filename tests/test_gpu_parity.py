@@ -242,3 +242,32 @@ def test_full_size_grid3d_400(arrow):
     Yrs = Yr[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
     c = np.sum(Yrs * R, axis=0) / np.sum(R * R, axis=0)
     assert err_inf(Yrs, R * c) <= 1e-5 * 20
+
+
+def test_full_size_rmat23_gcn_bf16(arrow):
+    """R-MAT scale 23 (n = 8.39M), symmetrised, self-loops, GCN-normalised; b = 8192; k = 128;
+    8 iterations in BF16 storage with FP32 accumulation and in FP32.
+
+    A . d^{1/2} = d^{1/2} holds for the GCN normalisation at any size, so a column set to
+    d^{1/2} must come back unchanged: within 1e-5 * iters (inf-norm, relative) in FP32 and
+    2e-2 (normwise) in BF16; the other columns of the two paths agree normwise within 2e-2.
+    """
+    A = w.rmat_gcn(23, 16, seed=5)
+    assert A.n == 1 << 23
+    M16 = arrow.ArrowMatrix(A, 8192, value_dtype="bf16")
+    M32 = M16.copy("f32")
+    assert M16.stats()["long_rows"] > 0
+    X = w.features(A.n, 128, seed=6)
+    d = np.sqrt(np.diff(A.rowptr).astype(np.float64))
+    X[:, 0] = d
+    del A
+    Xf = torch.from_numpy(X).cuda()
+    del X
+    iters = 8
+    Yf = M32.spmm(Xf, iters)
+    Yb = M16.spmm(Xf.bfloat16(), iters).float()
+    dd = torch.from_numpy(d).cuda()
+    assert float((Yf[:, 0].double() - dd).abs().max() / dd.max()) <= 1e-5 * iters
+    assert float(torch.linalg.vector_norm(Yb[:, 0].double() - dd) / torch.linalg.vector_norm(dd)) <= 2e-2
+    rel = torch.linalg.vector_norm(Yb - Yf, dim=0) / torch.linalg.vector_norm(Yf, dim=0)
+    assert float(rel.max()) <= 2e-2
