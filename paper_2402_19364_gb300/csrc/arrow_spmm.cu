@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] *= scl[v];
             const uint4 out = P::from_float(acc);
-            *reinterpret_cast<uint4*>(Y + int64_t(r0 + j) * a.ldx) = out;
+            st_y(Y + int64_t(r0 + j) * a.ldx, out);
             if (RESCALE) {
                 float yr[V];
                 P::to_float(out, yr);
@@ -1056,7 +1056,7 @@ int arrow_get_tuning(arrow_handle h, arrow_tuning* t) {
 int arrow_set_tuning(arrow_handle h, const arrow_tuning* t) {
     if (!h || !t) { set_error("arrow_set_tuning: NULL argument"); return ARROW_EINVAL; }
     if (t->tile_rows < 32 || t->tile_rows > kMaxTileRows || t->tile_nnz < kMinTileNnz || t->tile_nnz > kMaxTileNnz ||
-        t->ctas_per_sm < 1 || t->ctas_per_sm > 3 || t->carveout < 0 || t->carveout > 100) {
+        t->ctas_per_sm < 1 || t->ctas_per_sm > ARROW_ROWS_MIN_BLOCKS || t->carveout < 0 || t->carveout > 100) {
         set_error("arrow_set_tuning: value out of range");
         return ARROW_EINVAL;
     }

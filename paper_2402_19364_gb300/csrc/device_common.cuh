@@ -82,6 +82,18 @@ __device__ __forceinline__ uint4 ld_x(const void* p) {
                  : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
     return r;
 }
+// Output rows are written once per iteration and read by the next one, far beyond L2: by
+// default a plain store; ARROW_Y_STORE_CS selects the streaming (evict-first) form.
+#ifndef ARROW_Y_STORE_CS
+#define ARROW_Y_STORE_CS 0
+#endif
+__device__ __forceinline__ void st_y(void* p, const uint4& v) {
+#if ARROW_Y_STORE_CS
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+#else
+    *reinterpret_cast<uint4*>(p) = v;
+#endif
+}
 __device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
     int32_t r;
     asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(r) : "l"(p));
