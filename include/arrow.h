@@ -80,8 +80,9 @@ int arrow_opts_default(arrow_opts* o);
 /* ---- launch tuning -------------------------------------------------------------------- */
 /* How the fused row program is cut and launched (not in the paper; a property of this GPU
  * path): rows per tile, entries per tile (>= 1024, so every unsplit row fits), resident CTAs
- * per SM of the persistent rows kernel (1..3) and the shared-memory carveout in percent.
- * Defaults: 384, 3072, 3, 75. */
+ * per SM of the persistent rows kernel (1..4; with ARROW_RESCALE at most 3 are used, the
+ * register bound of that variant) and the shared-memory carveout in percent.
+ * Defaults: 256, 2048, 4, 70. */
 typedef struct {
     int32_t tile_rows;
     int32_t tile_nnz;
@@ -97,11 +98,11 @@ int arrow_get_tuning(arrow_handle h, arrow_tuning* t);
 
 /* Re-tile the handle (host, O(n)) and, if uploaded, replace its device tile tables; waits for
  * the device first.  Errors: ARROW_EINVAL (out of range: 32 <= tile_rows <= 2048,
- * 1024 <= tile_nnz <= 16384, 1 <= ctas_per_sm <= 3, 0 <= carveout <= 100), ARROW_ECUDA. */
+ * 1024 <= tile_nnz <= 16384, 1 <= ctas_per_sm <= 4, 0 <= carveout <= 100), ARROW_ECUDA. */
 int arrow_set_tuning(arrow_handle h, const arrow_tuning* t);
 
 /* arrow_autotune -- time a fixed set of tunings (tile shapes 128/1024, 256/2048, 384/3072,
- * 512/4096 rows/entries x 2 or 3 CTAs per SM, carveout fitted to them) with arrow_spmm on the
+ * 512/4096 rows/entries x 2..4 CTAs per SM that fit, carveout fitted to them) with arrow_spmm on the
  * caller's X, Y (as arrow_spmm) for `iters` iterations each (one warm-up call, two timed),
  * keep the fastest on the handle, and return it with its milliseconds per call.  Synchronises
  * `stream`.  Errors: as arrow_spmm and arrow_set_tuning. */

@@ -16,10 +16,10 @@ void set_error(const std::string& msg);
 // each (arrow_set_tuning / arrow_autotune change them per handle).  A tile's row pointers and
 // entries are staged into shared memory with bulk copies.
 #ifndef ARROW_TILE_NNZ
-#define ARROW_TILE_NNZ 3072
+#define ARROW_TILE_NNZ 2048
 #endif
 #ifndef ARROW_TILE_ROWS
-#define ARROW_TILE_ROWS 384
+#define ARROW_TILE_ROWS 256
 #endif
 constexpr int kTileRows = ARROW_TILE_ROWS;
 constexpr int kTileNnz = ARROW_TILE_NNZ;
@@ -88,7 +88,7 @@ struct arrow_handle_s {
     std::vector<int32_t> long_rows, long_segptr, seg_begin, seg_end;
     std::vector<int32_t> tile_row, tile_ent;
     int32_t long_row = arrow::kDefaultLongRow;
-    arrow_tuning tune{arrow::kTileRows, arrow::kTileNnz, 3, 75};
+    arrow_tuning tune{arrow::kTileRows, arrow::kTileNnz, 4, 70};
     double decompose_seconds = 0.0;
     bool uploaded = false;
     arrow::DeviceData dev;

@@ -39,10 +39,14 @@ namespace arrow {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
-// CTAs of the rows kernel that fit an SM by registers (launch bound); arrow_tuning's
-// ctas_per_sm stays at or below it.
+// CTAs of the rows kernel that fit an SM by registers (launch bounds): 4 for the plain
+// product, 3 with the FP64 rescale (its norm sums need more registers; at 4 it spills).
+// arrow_tuning's ctas_per_sm is capped by the variant's bound at launch.
 #ifndef ARROW_ROWS_MIN_BLOCKS
-#define ARROW_ROWS_MIN_BLOCKS 3
+#define ARROW_ROWS_MIN_BLOCKS 4
+#endif
+#ifndef ARROW_ROWS_MIN_BLOCKS_RESCALE
+#define ARROW_ROWS_MIN_BLOCKS_RESCALE 3
 #endif
 
 // ------------------------------------------------------------------------------------
@@ -85,7 +89,8 @@ __device__ __forceinline__ void issue_tile(const RowArgs& a, int t, unsigned cha
 // their 16-byte X gathers together, accumulates in FP32 in entry order (levels in order),
 // scales, stores the row and, with RESCALE, adds its squares to FP64 per-column sums.
 template <typename TX, typename TV, int T, bool RESCALE>
-__global__ void __launch_bounds__(256, ARROW_ROWS_MIN_BLOCKS) arrow_rows_kernel(RowArgs a) {
+__global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE : ARROW_ROWS_MIN_BLOCKS)
+    arrow_rows_kernel(RowArgs a) {
     using P = Pack<TX>;
     constexpr int V = P::V;
     constexpr int VE = 16 / int(sizeof(TV));
@@ -239,13 +244,12 @@ struct SegArgs {
     float* partials;   // [n_seg][kc]
 };
 
-// One warp per segment of a split row; the warp's teams stride over the entries and are
-// combined with a fixed xor butterfly (first stage of the deterministic head-row reduction).
+// One warp per segment of a split row (segment_partial), teams combined with a fixed xor
+// butterfly (first stage of the deterministic head-row reduction).
 template <typename TX, typename TV, int T>
 __global__ void __launch_bounds__(256) arrow_segments_kernel(SegArgs a) {
     using P = Pack<TX>;
     constexpr int V = P::V;
-    constexpr int TPW = 32 / T;
     const int lane = threadIdx.x & 31;
     const int tl = lane & (T - 1);
     const int tw = lane / T;
@@ -257,35 +261,7 @@ __global__ void __launch_bounds__(256) arrow_segments_kernel(SegArgs a) {
     for (int64_t g = warp0; g < a.n_seg; g += nwarps) {
         const int32_t s = __ldg(a.seg_begin + g), e = __ldg(a.seg_end + g);
         float acc[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = 0.f;
-        int32_t j = s + tw;
-        for (; j + 3 * TPW < e; j += 4 * TPW) {
-            int32_t c[4];
-            float w[4];
-            uint4 x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) c[u] = ld_stream_i32(a.col + j + u * TPW);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) w[u] = val_to_float(ld_stream_val<TV>(val + j + u * TPW));
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = ld_x(X + int64_t(c[u]) * a.ldx);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                float f[V];
-                P::to_float(x[u], f);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = fmaf(w[u], f[v], acc[v]);
-            }
-        }
-        for (; j < e; j += TPW) {
-            const int32_t c = ld_stream_i32(a.col + j);
-            const float w = val_to_float(ld_stream_val<TV>(val + j));
-            float f[V];
-            P::to_float(ld_x(X + int64_t(c) * a.ldx), f);
-#pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = fmaf(w, f[v], acc[v]);
-        }
+        segment_partial<TX, TV, T>(a.col, val, X, a.ldx, s, e, lane, acc);
 #pragma unroll
         for (int off = T; off < 32; off <<= 1)
 #pragma unroll
@@ -649,9 +625,11 @@ static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags,
     }
     p.kc = p.T * p.V;
     const int sm = h->dev.sm_count > 0 ? h->dev.sm_count : 1;
-    // persistent rows kernel: ctas_per_sm CTAs per SM (one FP64 norm slot each)
+    // persistent rows kernel: ctas_per_sm CTAs per SM, capped by the variant's register bound
+    // (one FP64 norm slot each)
     const int64_t n_tiles = h->tile_row.empty() ? 0 : int64_t(h->tile_row.size()) - 1;
-    p.rows_grid = int(std::max<int64_t>(1, std::min<int64_t>(n_tiles, int64_t(sm) * h->tune.ctas_per_sm)));
+    const int cap = (flags & ARROW_RESCALE) ? ARROW_ROWS_MIN_BLOCKS_RESCALE : ARROW_ROWS_MIN_BLOCKS;
+    p.rows_grid = int(std::max<int64_t>(1, std::min<int64_t>(n_tiles, int64_t(sm) * std::min(h->tune.ctas_per_sm, cap))));
     const int64_t n_long = int64_t(h->long_rows.size());
     const int64_t teams = 256 / p.T;
     p.comb_grid = n_long ? int(std::max<int64_t>(1, std::min<int64_t>((n_long + teams - 1) / teams, int64_t(sm) * 2))) : 0;
@@ -1095,9 +1073,11 @@ int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t it
     arrow_tuning bt = h->tune;
     int rc = ARROW_OK;
     for (auto& sh : shapes) {
-        for (int ctas = 2; ctas <= 3 && rc == ARROW_OK; ++ctas) {
+        for (int ctas = 2; ctas <= ARROW_ROWS_MIN_BLOCKS && rc == ARROW_OK; ++ctas) {
+            if ((flags & ARROW_RESCALE) && ctas > ARROW_ROWS_MIN_BLOCKS_RESCALE) break;
             const TileLayout L = tile_layout(sh[0], sh[1]);
             const int per = rows_smem_bytes(L, 128) + 1024;
+            if (ctas * per > 227 * 1024) break;
             const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);
             arrow_tuning cand{sh[0], sh[1], ctas, pct};
             if ((rc = arrow_set_tuning(h, &cand))) break;

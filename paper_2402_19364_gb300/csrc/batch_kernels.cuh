@@ -160,11 +160,30 @@ inline void prepare_batch_rows(int carveout) {
     last = carveout;
 }
 
-// One warp per split-row segment of any matrix (first stage of the head-row reduction).
-template <typename TX, typename TV>
-__global__ void __launch_bounds__(256) arrow_batch_segments_kernel(BatchArgs a) {
+// One warp per split-row segment of any matrix (first stage of the head-row reduction): the
+// same arithmetic as arrow_segments_kernel, dispatched on the matrix's team width.
+template <typename TX, typename TV, int T>
+__device__ __forceinline__ void batch_segment(const MatDesc& d, int64_t g, int par, int lane) {
     using P = Pack<TX>;
     constexpr int V = P::V;
+    const int tl = lane & (T - 1), tw = lane / T;
+    const TX* __restrict__ X = static_cast<const TX*>(par ? d.xb : d.xa) + tl * V;
+    const int32_t s = __ldg(d.seg_begin + g), e = __ldg(d.seg_end + g);
+    float acc[V];
+    segment_partial<TX, TV, T>(d.lcol, static_cast<const TV*>(d.lval), X, d.k, s, e, lane, acc);
+#pragma unroll
+    for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+    if (tw == 0) {
+        float4* p = reinterpret_cast<float4*>(d.partials + g * d.k + tl * V);
+#pragma unroll
+        for (int q = 0; q < V / 4; ++q) p[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+}
+
+template <typename TX, typename TV>
+__global__ void __launch_bounds__(256) arrow_batch_segments_kernel(BatchArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -172,28 +191,14 @@ __global__ void __launch_bounds__(256) arrow_batch_segments_kernel(BatchArgs a) 
         const int m = find_mat(a.base, a.n_mats, w);
         const MatDesc& d = a.d[m];
         const int64_t g = w - a.base[m];
-        const int T = d.T, tpw = 32 / T, tl = lane & (T - 1), tw = lane / T;
-        const TX* __restrict__ X = static_cast<const TX*>((a.parity ^ d.flip) ? d.xb : d.xa) + tl * V;
-        const TV* __restrict__ val = static_cast<const TV*>(d.lval);
-        const int32_t s = __ldg(d.seg_begin + g), e = __ldg(d.seg_end + g);
-        float acc[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = 0.f;
-        for (int32_t j = s + tw; j < e; j += tpw) {
-            const int32_t c = ld_stream_i32(d.lcol + j);
-            const float wv = val_to_float(ld_stream_val<TV>(val + j));
-            float f[V];
-            P::to_float(ld_x(X + int64_t(c) * d.k), f);
-#pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = fmaf(wv, f[v], acc[v]);
-        }
-        for (int off = T; off < 32; off <<= 1)
-#pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
-        if (tw == 0) {
-            float4* p = reinterpret_cast<float4*>(d.partials + g * d.k + tl * V);
-#pragma unroll
-            for (int q = 0; q < V / 4; ++q) p[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        const int par = a.parity ^ d.flip;
+        switch (d.T) {
+            case 1: batch_segment<TX, TV, 1>(d, g, par, lane); break;
+            case 2: batch_segment<TX, TV, 2>(d, g, par, lane); break;
+            case 4: batch_segment<TX, TV, 4>(d, g, par, lane); break;
+            case 8: batch_segment<TX, TV, 8>(d, g, par, lane); break;
+            case 16: batch_segment<TX, TV, 16>(d, g, par, lane); break;
+            default: batch_segment<TX, TV, 32>(d, g, par, lane); break;
         }
     }
 }

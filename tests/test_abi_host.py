@@ -151,7 +151,7 @@ def test_fused_program_stats(arrow):
     deg = np.diff(A.rowptr)
     assert s["long_rows"] == int((deg > 32).sum())
     assert s["segments"] == int(np.sum((deg[deg > 32] + 63) // 64))
-    assert s["tiles"] >= (A.n + 383) // 384                  # at most 384 rows per tile
+    assert s["tiles"] >= (A.n + 255) // 256                  # at most 256 rows per tile
 
 
 def test_save_load_roundtrip_and_corruption(arrow, tmp_path):
@@ -186,12 +186,12 @@ def test_tuning_retiles_and_validates(arrow):
     A = w.grid3d(30)
     M = arrow.ArrowMatrix(A, 256, host_only=True)
     t = M.tuning
-    assert (t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"]) == (384, 3072, 3, 75)
+    assert (t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"]) == (256, 2048, 4, 70)
     n_default = M.stats()["tiles"]
     M.set_tuning(128, 1024, 2, 50)
     assert M.tuning["tile_rows"] == 128 and M.stats()["tiles"] > n_default
     assert M.stats()["tiles"] >= (A.n + 127) // 128
-    for bad in ((16, 1024, 2, 50), (128, 512, 2, 50), (128, 1024, 4, 50), (128, 1024, 2, 101), (4096, 1024, 2, 50)):
+    for bad in ((16, 1024, 2, 50), (128, 512, 2, 50), (128, 1024, 5, 50), (128, 1024, 2, 101), (4096, 1024, 2, 50)):
         with pytest.raises(arrow.ArrowError):
             M.set_tuning(*bad)
     assert M.tuning["tile_rows"] == 128                      # unchanged after rejected values
