@@ -65,7 +65,7 @@ void enqueue_typed(arrow_batch_s* B, int iters, cudaStream_t s) {
         rows_max = std::max(rows_max, h->tune.tile_rows);
         nnz_max = std::max(nnz_max, h->tune.tile_nnz);
     }
-    if (!B->hs.empty()) { ctas = std::min(B->hs[0]->tune.ctas_per_sm, 3); carve = B->hs[0]->tune.carveout; }
+    if (!B->hs.empty()) { ctas = std::min(B->hs[0]->tune.ctas_per_sm, kBatchMinBlocks); carve = B->hs[0]->tune.carveout; }
     const TileLayout L = tile_layout(rows_max, nnz_max);
     auto args = [&](int cls, int parity, int dir) {
         return BatchArgs{B->d_desc, bases[cls], int32_t(n_m), tot[cls], parity, dir, B->d_status, L.rp, L.col, L.buf};
@@ -284,7 +284,7 @@ int arrow_batch_autotune(arrow_batch B, const void* const* X, void* const* Y, co
         return int(ARROW_OK);
     };
     for (auto& sh : shapes) {
-        for (int ctas = 2; ctas <= 3; ++ctas) {
+        for (int ctas = 2; ctas <= kBatchMinBlocks; ++ctas) {
             const TileLayout L = tile_layout(sh[0], sh[1]);
             const int per = batch_smem_bytes(L) + 1024;
             const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);

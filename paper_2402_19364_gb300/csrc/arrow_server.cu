@@ -142,7 +142,7 @@ void launch_step(arrow_server_s* S, const int64_t* tot, int n_m, cudaStream_t s)
         nnz_max = std::max(nnz_max, r.h->tune.tile_nnz);
     }
     const TileLayout L = tile_layout(rows_max, nnz_max);
-    const int ctas = S->active.empty() ? 3 : std::min(S->active[0].h->tune.ctas_per_sm, 3);
+    const int ctas = S->active.empty() ? 3 : std::min(S->active[0].h->tune.ctas_per_sm, kBatchMinBlocks);
     const int carve = S->active.empty() ? 75 : S->active[0].h->tune.carveout;
     auto args = [&](int cls, int parity, int dir) {
         return BatchArgs{S->d_desc, db + cls * (n_m + 1), n_m, tot[cls], parity, dir, S->d_status, L.rp, L.col, L.buf};

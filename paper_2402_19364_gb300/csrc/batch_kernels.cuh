@@ -57,8 +57,16 @@ inline int batch_smem_bytes(const TileLayout& L) { return 128 + kStages * L.buf;
 
 // Rows of every matrix's tiles (the fused arrow-row kernel of arrow_spmm with a per-tile
 // matrix descriptor and a run-time team width); same tile pipeline without block barriers.
+// Entries per gather round of a row (all of a round's gathers are in flight together) and the
+// resident CTAs per SM that the register use allows.
+#ifndef ARROW_BATCH_ROUND
+#define ARROW_BATCH_ROUND 8
+#endif
+constexpr int kBatchRound = ARROW_BATCH_ROUND;
+constexpr int kBatchMinBlocks = kBatchRound > 8 ? 2 : 3;
+
 template <typename TX, typename TV>
-__global__ void __launch_bounds__(256, 3) arrow_batch_rows_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(256, kBatchMinBlocks) arrow_batch_rows_kernel(BatchArgs a) {
     using P = Pack<TX>;
     constexpr int V = P::V;
     constexpr int VE = 16 / int(sizeof(TV));
@@ -118,14 +126,14 @@ __global__ void __launch_bounds__(256, 3) arrow_batch_rows_kernel(BatchArgs a) {
             float acc[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.f;
-            for (int base = s; base < e; base += 8) {
+            for (int base = s; base < e; base += kBatchRound) {
                 const int cnt = e - base;
-                uint4 x[8];
+                uint4 x[kBatchRound];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
+                for (int u = 0; u < kBatchRound; ++u)
                     if (u < cnt) x[u] = ld_x(X + int64_t(scol[base + u]) * ldx);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
+                for (int u = 0; u < kBatchRound; ++u) {
                     if (u < cnt) {
                         const float wv = val_to_float(sval[base + u]);
                         float f[V];
