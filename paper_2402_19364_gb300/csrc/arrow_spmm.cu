@@ -52,9 +52,9 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 // ------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------
-// dynamic shared memory: pipeline state, kStages tile buffers, per-warp FP64 column sums
-// of squares (8 warps x kc doubles)
-static inline int rows_smem_bytes(const TileLayout& L, int kc) { return 128 + kStages * L.buf + 8 * kc * 8; }
+// dynamic shared memory: pipeline state, kStages tile buffers and, with the rescale, the
+// per-team FP64 column sums of squares (256 / T teams x kc = T V columns: 256 V doubles)
+static inline int rows_smem_bytes(const TileLayout& L, int norm_doubles) { return 128 + kStages * L.buf + 8 * norm_doubles; }
 
 struct RowArgs {
     const int32_t* rowptr;     // short-row stream
@@ -99,9 +99,8 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
     extern __shared__ __align__(128) unsigned char smem[];
     PipeSmem* ps = reinterpret_cast<PipeSmem*>(smem);
     unsigned char* bufs = smem + 128;
-    double* wsum = reinterpret_cast<double*>(smem + 128 + kStages * a.buf_bytes);   // [8][kc]
+    double* wsum = reinterpret_cast<double*>(smem + 128 + kStages * a.buf_bytes);   // [TEAMS][kc]
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
     const int tl = threadIdx.x & (T - 1);
     const int team = threadIdx.x / T;
     const int col0 = tl * V;
@@ -119,7 +118,7 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
         fence_mbar_init();
     }
     if (RESCALE)
-        for (int c = threadIdx.x; c < 8 * a.kc; c += blockDim.x) wsum[c] = 0.0;
+        for (int c = threadIdx.x; c < TEAMS * a.kc; c += blockDim.x) wsum[c] = 0.0;
     __syncthreads();
     if (threadIdx.x == 0)
         for (int b = 0; b < kStages; ++b)
@@ -181,18 +180,11 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
                 for (int v = 0; v < V; ++v) sq[v] = fmaf(yr[v], yr[v], sq[v]);
             }
         }
-        if (RESCALE) {
-            // this tile's squares: teams of the warp (fixed xor butterfly, FP32), then the
-            // warp's FP64 running sum in shared memory
+        if (RESCALE && (i & 7) == 7) {
+            // every 8 tiles each lane adds its FP32 squares to its team's FP64 column sums
+            // (the lane owns these columns of the slot: no other thread touches them)
 #pragma unroll
-            for (int off = T; off < 32; off <<= 1)
-#pragma unroll
-                for (int v = 0; v < V; ++v) sq[v] += __shfl_xor_sync(0xffffffffu, sq[v], off);
-            if (lane < T)
-#pragma unroll
-                for (int v = 0; v < V; ++v) wsum[warp * a.kc + col0 + v] += double(sq[v]);
-#pragma unroll
-            for (int v = 0; v < V; ++v) sq[v] = 0.f;
+            for (int v = 0; v < V; ++v) { wsum[team * a.kc + col0 + v] += double(sq[v]); sq[v] = 0.f; }
         }
         __syncwarp();
         if (lane == 0)
@@ -204,16 +196,19 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
                 }
             });
     }
+    if (RESCALE)
+#pragma unroll
+        for (int v = 0; v < V; ++v) wsum[team * a.kc + col0 + v] += double(sq[v]);
     __syncthreads();
     if (ps->failed) {
         if (threadIdx.x == 0) drain_pipeline(ps);
         return;
     }
     if (RESCALE) {
-        // block's FP64 column sums: warps in fixed order
+        // block's FP64 column sums: teams in fixed order
         for (int c = threadIdx.x; c < a.kc; c += blockDim.x) {
             double acc = 0.0;
-            for (int w = 0; w < 8; ++w) acc += wsum[w * a.kc + c];
+            for (int t2 = 0; t2 < TEAMS; ++t2) acc += wsum[t2 * a.kc + c];
             a.norm_partials[int64_t(blockIdx.x) * a.ldx + a.koff + c] = acc;
         }
     }
@@ -660,7 +655,7 @@ static void launch_step(const arrow_handle_s* h, const Plan& p, const TX* cur, T
         const TileLayout L = tile_layout(h->tune.tile_rows, h->tune.tile_nnz);
         RowArgs ra{d.rowptr, d.col, d.val, d.tile_row, d.tile_ent, n_tiles, cur, nxt, k, koff, p.kc, scale_in, np,
                    d.status, L.rp, L.col, L.buf};
-        const int smem = rows_smem_bytes(L, p.kc);
+        const int smem = rows_smem_bytes(L, np ? (256 / T) * p.kc : 0);
         cudaEvent_t e0 = pf.begin();
         if (np) {
             set_smem_attrs(reinterpret_cast<const void*>(arrow_rows_kernel<TX, TV, T, true>), h->tune.carveout);
@@ -1038,7 +1033,7 @@ int arrow_set_tuning(arrow_handle h, const arrow_tuning* t) {
         set_error("arrow_set_tuning: value out of range");
         return ARROW_EINVAL;
     }
-    if (rows_smem_bytes(tile_layout(t->tile_rows, t->tile_nnz), 256) > 227 * 1024) {
+    if (rows_smem_bytes(tile_layout(t->tile_rows, t->tile_nnz), 256 * 8) > 227 * 1024) {
         set_error("arrow_set_tuning: tile too large for shared memory");
         return ARROW_EINVAL;
     }
@@ -1076,7 +1071,7 @@ int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t it
         for (int ctas = 2; ctas <= ARROW_ROWS_MIN_BLOCKS && rc == ARROW_OK; ++ctas) {
             if ((flags & ARROW_RESCALE) && ctas > ARROW_ROWS_MIN_BLOCKS_RESCALE) break;
             const TileLayout L = tile_layout(sh[0], sh[1]);
-            const int per = rows_smem_bytes(L, 128) + 1024;
+            const int per = rows_smem_bytes(L, (flags & ARROW_RESCALE) ? 256 * int(16 / dtype_size(x_dtype)) : 0) + 1024;
             if (ctas * per > 227 * 1024) break;
             const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);
             arrow_tuning cand{sh[0], sh[1], ctas, pct};
