@@ -50,7 +50,19 @@ def parse():
     p.add_argument("--no-cusparse", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--tuning", default="", help="tile_rows,tile_nnz,ctas_per_sm,carveout: fixed rows-kernel tuning "
+                   "instead of autotuning (keeps a profiler's launch list short)")
     return p.parse_args()
+
+
+def fixed_tuning(a):
+    """The --tuning value as a 4-tuple, or None (autotune)."""
+    if not a.tuning:
+        return None
+    t = tuple(int(v) for v in a.tuning.split(","))
+    if len(t) != 4:
+        raise SystemExit("--tuning wants tile_rows,tile_nnz,ctas_per_sm,carveout")
+    return t
 
 
 def workload_spec(a):
@@ -288,7 +300,12 @@ def run_batch(a):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
-    tuned, tuned_ms = B.autotune(X16, iters, outs=Y16)
+    if fixed_tuning(a):
+        for m in mats16:
+            m.set_tuning(*fixed_tuning(a))
+        tuned = mats16[0].tuning
+    else:
+        tuned, tuned_ms = B.autotune(X16, iters, outs=Y16)
     t_tune = time.perf_counter() - t0
     for _ in range(max(3, a.warmup)):
         B.spmm(X16, iters, outs=Y16, graph=True)
@@ -487,7 +504,11 @@ def main():
     stream = torch.cuda.current_stream()
 
     t0 = time.perf_counter()
-    tuned, _ = M.autotune(Xd, iters, rescale=spec["rescale"], out=Yd)   # arrow_autotune keeps the fastest
+    if fixed_tuning(a):
+        M.set_tuning(*fixed_tuning(a))
+        tuned = M.tuning
+    else:
+        tuned, _ = M.autotune(Xd, iters, rescale=spec["rescale"], out=Yd)   # arrow_autotune keeps the fastest
     t_tune = time.perf_counter() - t0
     for _ in range(max(3, a.warmup)):
         M.spmm(Xd, iters, rescale=spec["rescale"], out=Yd)
