@@ -114,10 +114,22 @@ def grid_stencil(dims, seed: int | None = 1, value_range=(0.5, 1.5), row_normali
     return Csr(n, rowptr, colidx, _round_values(vals, round_to))
 
 
+def _sorted_unique(a: np.ndarray) -> np.ndarray:
+    """np.unique of a 1-D integer array by sort + neighbour test (the same result; np.unique's
+    own path is far slower on arrays of hundreds of millions of keys)."""
+    a = np.sort(a)
+    if a.size < 2:
+        return a
+    m = np.empty(a.size, dtype=bool)
+    m[0] = True
+    np.not_equal(a[1:], a[:-1], out=m[1:])
+    return a[m]
+
+
 def _csr_from_pairs(n: int, rows: np.ndarray, cols: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     """Pattern CSR (rowptr int64, colidx int32) from (row, col) pairs; duplicates removed."""
     key = rows.astype(np.int64) * n + cols.astype(np.int64)
-    key = np.unique(key)
+    key = _sorted_unique(key)
     r = key // n
     c = (key % n).astype(np.int32)
     rowptr = np.zeros(n + 1, dtype=np.int64)
@@ -135,19 +147,20 @@ def rmat_edges(scale: int, edge_factor: int, abcd=(0.57, 0.19, 0.19, 0.05), seed
     n = 1 << scale
     m = edge_factor * n
     rng = np.random.Generator(np.random.PCG64(seed))
-    u = np.zeros(m, dtype=np.int64)
-    v = np.zeros(m, dtype=np.int64)
+    wide = np.int64 if scale > 31 else np.uint32
+    u = np.zeros(m, dtype=wide)
+    v = np.zeros(m, dtype=wide)
     ab = a + b
     abc = a + b + c
     for lvl in range(scale):
         r = rng.random(m, dtype=np.float32)
-        bit = 1 << (scale - 1 - lvl)
+        bit = wide(1 << (scale - 1 - lvl))
         # quadrant: [0,a) -> (0,0); [a,a+b) -> (0,1); [a+b,a+b+c) -> (1,0); else (1,1)
         row_bit = r >= ab
         col_bit = ((r >= a) & (r < ab)) | (r >= abc)
         u += row_bit * bit
         v += col_bit * bit
-    return n, u, v
+    return n, u.astype(np.int64), v.astype(np.int64)
 
 
 def rmat_gcn(scale: int, edge_factor: int = 16, abcd=(0.57, 0.19, 0.19, 0.05), seed: int = 5,
