@@ -113,9 +113,14 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_traffic():
+def workload_key(spec) -> str:
+    """Short name of a single-matrix workload, as the traffic file records it."""
+    return f"{spec['name']} N={spec['N']} k={spec['k']} {spec['dtype']} rescale={int(spec['rescale'])}"
+
+
+def kernel_traffic(workload: str):
     """DRAM bytes per rows-kernel launch from the committed ncu summary, if it was taken on
-    the current kernel source (profiles/arrow_rows_traffic.txt); else None."""
+    the current kernel source and on this workload (profiles/arrow_rows_traffic.txt); else None."""
     path = os.path.join(ROOT, "profiles", "arrow_rows_traffic.txt")
     try:
         with open(KERNEL_SRC, "rb") as f:
@@ -126,7 +131,7 @@ def kernel_traffic():
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_sha256_16") != digest:
+        if kv.get("kernel_source_sha256_16") != digest or kv.get("workload") != workload:
             return None
         return kv
     except Exception:
@@ -543,7 +548,7 @@ def main():
     peak, peak_kind = load_peaks()
     per_launch_s = (rows_ms + seg_ms) / max(1, rows_launches) / 1e3
     achieved = ab["total"] / per_launch_s / 1e9
-    tr = kernel_traffic()
+    tr = kernel_traffic(workload_key(spec))
     traffic = None
     if tr is not None:
         try:
