@@ -301,13 +301,14 @@ def run_batch(a):
     Y16 = [torch.empty_like(x) for x in X16]
     X32 = [x.float() for x in X16]
     Y32 = [torch.empty_like(x) for x in X32]
+    if fixed_tuning(a):
+        for m in mats16:
+            m.set_tuning(*fixed_tuning(a))
     B = arrow.ArrowBatch(mats16)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     if fixed_tuning(a):
-        for m in mats16:
-            m.set_tuning(*fixed_tuning(a))
         tuned = mats16[0].tuning
     else:
         tuned, tuned_ms = B.autotune(X16, iters, outs=Y16)
@@ -526,14 +527,17 @@ def main():
     barrier(pg)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     e0.record(stream)
-    for _ in range(a.steps):
+    for i in range(a.steps):
         M.spmm(Xd, iters, rescale=spec["rescale"], out=Yd, profile=True)
+        marks[i].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(pg)
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
+    step_ms = [(marks[i - 1] if i else e0).elapsed_time(marks[i]) for i in range(a.steps)]
     ms_total = max_over_ranks(pg, ms_total)
     rows_ms, rows_launches = M.profile_get(arrow.ARROW_K_ROWS)
     seg_ms, seg_launches = M.profile_get(arrow.ARROW_K_SEGMENTS)
@@ -562,7 +566,9 @@ def main():
                 "frac_of_nominal_8000": achieved / 8000.0}
 
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": a.steps,
-           "warmup": max(3, a.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "warmup": max(3, a.warmup), "ms_per_step": ms_step,
+           "step_ms": {"mean": sum(step_ms) / len(step_ms), "min": min(step_ms), "max": max(step_ms)},
+           "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": dt_name, "data": "synthetic",
            "config": {"workload": spec["desc"], "n": A.n, "nnz": A.nnz, "b": spec["b"], "k": k, "iters": iters,
                       "rescale_fp64": spec["rescale"], "levels": [list(x) for x in levels],

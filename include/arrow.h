@@ -206,9 +206,12 @@ int arrow_spmm_static(arrow_handle h, const void* X, int64_t k, int32_t iters, v
 typedef struct arrow_batch_s* arrow_batch;   /* opaque, library-owned */
 
 /* arrow_batch_create -- group count uploaded handles (same device, same value dtype) so that
- * one call advances all of them.  The handles must outlive the batch.  Not in the paper (its
- * matrices are advanced by separate rank groups, Alg. 2); this is the one-GPU batching of many
- * independent problems.  Errors: ARROW_EINVAL, ARROW_ESTATE (a handle not uploaded), ARROW_ECUDA. */
+ * one call advances all of them.  The handles must outlive the batch.  A member handle may be
+ * re-tuned (arrow_set_tuning) or re-uploaded between batch calls: the next arrow_batch_spmm
+ * sees it, waits for its stream and rebuilds the batch's work-unit tables, descriptors and
+ * graph.  Not in the paper (its matrices are advanced by separate rank groups, Alg. 2); this
+ * is the one-GPU batching of many independent problems.  Errors: ARROW_EINVAL, ARROW_ESTATE
+ * (a handle not uploaded), ARROW_ECUDA. */
 int arrow_batch_create(const arrow_handle* handles, int32_t count, arrow_batch* out);
 
 /* arrow_batch_spmm -- for every matrix m: Y[m] = A_m^iters X[m] (sigma = identity), with

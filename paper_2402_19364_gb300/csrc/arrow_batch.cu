@@ -30,6 +30,7 @@ struct arrow_batch_s {
     int sm_count = 1;
     // prefix sums of work units per kernel class: tiles, segments, long rows, 32-row chunks
     std::vector<int64_t> base[4];
+    std::vector<uint64_t> gens;           // each handle's generation when base/descriptors were built
     int64_t* d_base = nullptr;            // the four prefix arrays, concatenated
     MatDesc* d_desc = nullptr;
     std::vector<MatDesc> h_desc;
@@ -108,7 +109,9 @@ void enqueue(arrow_batch_s* B, int x_dtype, int iters, cudaStream_t s) {
 // Prefix sums of every kernel class's work units over the batch's matrices, uploaded.
 cudaError_t upload_bases(arrow_batch_s* B) {
     for (auto& v : B->base) v.assign(1, 0);
+    B->gens.clear();
     for (arrow_handle_s* h : B->hs) {
+        B->gens.push_back(h->generation);
         const int64_t tiles = h->tile_row.empty() ? 0 : int64_t(h->tile_row.size()) - 1;
         B->base[0].push_back(B->base[0].back() + tiles);
         B->base[1].push_back(B->base[1].back() + int64_t(h->seg_begin.size()));
@@ -195,6 +198,19 @@ int arrow_batch_spmm(arrow_batch B, const void* const* X, void* const* Y, const 
         }
         const arrow_handle_s* h = B->hs[m];
         need += 2 * al256(size_t(h->n) * size_t(k[m]) * dsize(x_dtype)) + al256(std::max<size_t>(1, h->seg_begin.size()) * size_t(k[m]) * 4);
+    }
+    // a member handle re-tiled or re-uploaded since the batch last looked (arrow_set_tuning,
+    // arrow_upload): its work-unit counts and device pointers changed, so rebuild both (the
+    // re-tiling synchronised the device before it freed the old tables)
+    for (size_t m = 0; m < n_m; ++m) {
+        if (!B->hs[m]->uploaded) { set_error("arrow_batch_spmm: a member handle is no longer uploaded"); return ARROW_ESTATE; }
+        if (B->hs[m]->generation != B->gens[m]) {
+            BCK(cudaStreamSynchronize(s));
+            BCK(upload_bases(B));
+            B->key.clear();
+            if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+            break;
+        }
     }
     if (iters == 0) {
         for (size_t m = 0; m < n_m; ++m)

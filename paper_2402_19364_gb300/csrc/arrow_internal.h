@@ -91,6 +91,9 @@ struct arrow_handle_s {
     arrow_tuning tune{arrow::kTileRows, arrow::kTileNnz, 4, 70};
     double decompose_seconds = 0.0;
     bool uploaded = false;
+    // bumped whenever the device arrays or the tile table change (upload, re-tiling):
+    // batches that cached descriptors or work-unit counts of this handle rebuild them
+    uint64_t generation = 0;
     arrow::DeviceData dev;
     std::vector<arrow::ProfileRecord> prof;       // recorded, not yet read
     std::vector<void*> event_pool;                // free cudaEvent_t

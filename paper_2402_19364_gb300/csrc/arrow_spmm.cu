@@ -242,7 +242,7 @@ struct SegArgs {
 // One warp per segment of a split row (segment_partial), teams combined with a fixed xor
 // butterfly (first stage of the deterministic head-row reduction).
 template <typename TX, typename TV, int T>
-__global__ void __launch_bounds__(256) arrow_segments_kernel(SegArgs a) {
+__global__ void __launch_bounds__(256, ARROW_SEG_MIN_BLOCKS) arrow_segments_kernel(SegArgs a) {
     using P = Pack<TX>;
     constexpr int V = P::V;
     const int lane = threadIdx.x & 31;
@@ -863,6 +863,7 @@ int arrow_upload(arrow_handle h) {
     }
     if (rc != ARROW_OK) { free_device(h->dev); return rc; }
     h->uploaded = true;
+    h->generation++;
     return ARROW_OK;
 }
 
@@ -1052,6 +1053,7 @@ int arrow_set_tuning(arrow_handle h, const arrow_tuning* t) {
             if ((rc = upload_vec(&h->dev.tile_ent, h->tile_ent, bytes))) return rc;
         }
     }
+    if (std::memcmp(&h->tune, t, sizeof(*t)) != 0) h->generation++;   // batches pick the new launch shape up
     h->tune = *t;
     return ARROW_OK;
 }

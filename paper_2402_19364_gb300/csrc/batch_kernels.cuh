@@ -191,7 +191,7 @@ __device__ __forceinline__ void batch_segment(const MatDesc& d, int64_t g, int p
 }
 
 template <typename TX, typename TV>
-__global__ void __launch_bounds__(256) arrow_batch_segments_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(256, ARROW_SEG_MIN_BLOCKS) arrow_batch_segments_kernel(BatchArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;

@@ -159,6 +159,12 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 // address per team per load) and a team keeps U gathers in flight; lane tl of a team owns
 // columns tl*V .. tl*V+V-1.  (U = 8 measured faster than 4, and faster than coalesced index
 // slices handed out by shuffle, on an R-MAT scale 21 matrix at k = 128 BF16.)
+// Resident CTAs per SM that the split-row segment kernels are compiled for (launch bounds).
+// Without a bound the compiler fits them into 32 registers, too few to keep a team's U
+// gathers in flight together.
+#ifndef ARROW_SEG_MIN_BLOCKS
+#define ARROW_SEG_MIN_BLOCKS 4
+#endif
 template <typename TX, typename TV, int T, int U = 8>
 __device__ __forceinline__ void segment_partial(const int32_t* __restrict__ col, const TV* __restrict__ val,
                                                       const TX* __restrict__ X, int64_t ldx, int s, int e, int lane,

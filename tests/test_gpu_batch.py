@@ -131,3 +131,21 @@ def test_batch_autotune(arrow):
     assert t > 0 and all(m.tuning == best for m in ms)
     for y, r in zip(B.spmm(Xs, 4, graph=True), ref):
         assert torch.equal(y, r)
+
+
+def test_member_retuned_after_batch_creation(arrow):
+    # re-tiling a member handle changes its tile count and frees its old tile table; the
+    # batch must notice on its next call and rebuild its work-unit tables and descriptors
+    mats, ks = _rgg_batch(5, 21)
+    ms = [arrow.ArrowMatrix(A, int(np.ceil(np.sqrt(A.n))), value_dtype="f16") for A in mats]
+    Xs = [torch.from_numpy(w.features(A.n, k, seed=i)).to("cuda", torch.float16) for i, (A, k) in enumerate(zip(mats, ks))]
+    B = arrow.ArrowBatch(ms)
+    ref = [y.clone() for y in B.spmm(Xs, 3, graph=True)]
+    for shape in ((512, 4096, 3, 97), (128, 1024, 2, 40)):
+        for M in ms:
+            M.set_tuning(*shape)
+        for graph in (False, True):
+            Ys = B.spmm(Xs, 3, graph=graph)
+            torch.cuda.synchronize()
+            assert B.status() == 0
+            assert all(torch.equal(y, r) for y, r in zip(Ys, ref))
