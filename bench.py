@@ -8,8 +8,14 @@ Default workload (one step = one arrow_spmm call = the whole hot path once):
 Inputs (X 4.1 GB, A 3.6 GB) are larger than the 129 MB L2, so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload grid3d|grid2d|rmat] [--size S] [--iters T] [--k K] [--dtype f32|bf16]
+                  [--workload grid3d|grid2d|rmat|batch|serve] [--size S] [--iters T] [--k K]
+                  [--dtype f32|bf16] [--count M] [--tuning R,E,C,P] [--no-e2e] [--no-cpu] [--no-cusparse]
 
+The line carries the device-timed value, the rows kernel's roofline, per-step min/mean/max,
+the clocks seen during the timed region, an end-to-end figure through the public call with
+pinned host buffers (copies inside the timed region; two steps in flight on two streams,
+and the one-stream form beside it), cuSPARSE on the undecomposed matrix and the CPU oracle.
+The rows kernel is autotuned before timing unless --tuning fixes its launch configuration.
 --impl reference times the CPU oracle (the FP64 product of the oracle package, as it
 stands) on a bounded sample of the same workload on the host cores.
 Under torchrun each rank runs its own replica of the workload (weak scaling).
