@@ -1,0 +1,65 @@
+"""CPU tests of bench.py's host logic: workload specs, the traffic record's guards, peaks,
+the fixed-tuning option and the whole-job arithmetic (no GPU)."""
+import argparse
+import hashlib
+import os
+
+import pytest
+
+import bench
+
+
+def _args(**kw):
+    base = dict(workload="grid3d", size=0, k=0, iters=0, dtype="", tuning="")
+    base.update(kw)
+    return argparse.Namespace(**base)
+
+
+def test_default_workload_is_the_400_cubed_grid():
+    spec = bench.workload_spec(_args())
+    assert (spec["N"], spec["b"], spec["k"], spec["iters"], spec["rescale"], spec["dtype"]) == (400, 4096, 16, 20, True, "f32")
+    assert bench.workload_key(spec) == "grid3d N=400 k=16 f32 rescale=1"
+    r = bench.workload_spec(_args(workload="rmat"))
+    assert (r["N"], r["b"], r["k"], r["iters"], r["dtype"]) == (23, 8192, 128, 8, "bf16")
+
+
+def test_traffic_record_matches_source_and_workload():
+    spec = bench.workload_spec(_args())
+    tr = bench.kernel_traffic(bench.workload_key(spec))
+    with open(bench.KERNEL_SRC, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    if tr is None:
+        pytest.skip("traffic record taken on another kernel source")      # reported as null then
+    assert tr["kernel_source_sha256_16"] == digest
+    dram = float(tr["dram_bytes_per_launch_full_size"])
+    alg = float(tr["algorithmic_bytes_per_launch_full_size"])
+    assert dram == pytest.approx(float(tr["dram_bytes_read_per_launch_full_size"]) +
+                                 float(tr["dram_bytes_write_per_launch_full_size"]), rel=1e-6)
+    assert 0.5 < dram / alg < 1.5
+    # any other workload (or size) gets no traffic figure
+    for other in (_args(workload="rmat"), _args(size=200), _args(k=32)):
+        assert bench.kernel_traffic(bench.workload_key(bench.workload_spec(other))) is None
+
+
+def test_traffic_guard_rejects_a_changed_source(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("// another kernel\n")
+    monkeypatch.setattr(bench, "KERNEL_SRC", str(src))
+    assert bench.kernel_traffic("grid3d N=400 k=16 f32 rescale=1") is None
+
+
+def test_fixed_tuning_parse():
+    assert bench.fixed_tuning(_args()) is None
+    assert bench.fixed_tuning(_args(tuning="384,3072,3,85")) == (384, 3072, 3, 85)
+    with pytest.raises(SystemExit):
+        bench.fixed_tuning(_args(tuning="384,3072"))
+
+
+def test_peaks_and_job_value():
+    peak, kind = bench.load_peaks()
+    assert peak > 1000 and kind in ("measured", "fallback")
+    if os.path.exists(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")):
+        assert kind == "measured"
+    # whole-job throughput: every rank's units over the slowest rank's time
+    assert bench.job_value(20, 4, 100.0) == pytest.approx(800.0)
+    assert bench.max_over_ranks(None, 3.5) == 3.5
