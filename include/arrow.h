@@ -301,6 +301,27 @@ int arrow_level_perm(arrow_handle h, int32_t i, int32_t* perm_out);
  * nnz(B_i)); columns ascending in each row; values are A's float64 values. */
 int arrow_level_csr(arrow_handle h, int32_t i, int64_t* rowptr, int32_t* colidx, double* vals);
 
+/* Where the entries of B_i sit under the b x b tiling of Section 3.1 / Fig. 2: in the head
+ * rows or head columns (position < b; the part pruned towards the top and left corners in
+ * the discussion of the decomposition results, Section 6), or elsewhere (the diagonal tiles
+ * for ARROW_PRED_BLOCK, the band for ARROW_PRED_BAND), and how many distinct b x b tiles hold
+ * an entry.  head_nnz + band_nnz = nnz.  Host computation, O(nnz(A) + n). */
+typedef struct {
+    int64_t n_active;   /* as arrow_level_info */
+    int64_t nnz;        /* nnz(B_i) */
+    int64_t head_nnz;   /* entries (p, q) of B_i with p < b or q < b */
+    int64_t band_nnz;   /* the other entries of B_i */
+    int64_t tiles;      /* distinct (p / b, q / b) over the entries of B_i */
+} arrow_level_shape;
+/* Errors: ARROW_EINVAL (NULL argument, level out of range). */
+int arrow_get_level_shape(arrow_handle h, int32_t i, arrow_level_shape* out);
+
+/* Number of distinct non-zero b x b tiles of A in its own row and column order: the equally
+ * sized blocks a 1.5D distribution deals out, against which Section 6 counts the non-zero
+ * blocks of the decomposition.  A as for arrow_decompose (host CSR, read only); b >= 1.
+ * Errors: ARROW_EINVAL (bad CSR, b < 1, NULL tiles). */
+int arrow_count_tiles(const arrow_csr* A, int64_t b, int64_t* tiles);
+
 typedef struct {
     int64_t n, nnz, b;
     int32_t levels;

@@ -260,3 +260,27 @@ def la_decompose(A, b: int, seed: int = 0, predicate=pred_block, max_levels: int
         rows, cols, vals = rows[~take], cols[~take], vals[~take]  # step 4
         i += 1
     return levels
+
+
+def arrow_shape(rows, cols, b: int):
+    """Where entries at positions (rows, cols) sit under the b x b tiling of Section 3.1 /
+    Fig. 2: (entries in a head row or head column, the other entries, distinct non-zero
+    b x b tiles).  The first two are the 'pruned' part and the band that Section 6 reads off
+    the decompositions (Fig. 1); the tile count is what it compares against 1.5D blocks."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    head = (rows < b) | (cols < b)
+    tiles = {(int(r) // b, int(c) // b) for r, c in zip(rows, cols)}
+    return int(np.count_nonzero(head)), int(np.count_nonzero(~head)), len(tiles)
+
+
+def level_shape(L: Level):
+    """arrow_shape of the entries of B_i (positions of level i)."""
+    rows = np.repeat(np.arange(L.n, dtype=np.int64), np.diff(L.rowptr))
+    return arrow_shape(rows, L.colidx, L.b)
+
+
+def count_tiles(A, b: int) -> int:
+    """Distinct non-zero b x b tiles of A in its own order (equally sized 1.5D blocks)."""
+    rows = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.rowptr))
+    return arrow_shape(rows, A.colidx, b)[2]

@@ -16,7 +16,7 @@ from ._native import (ARROW_BF16, ARROW_F16, ARROW_F32, ARROW_GRAPH, ARROW_HOST_
                       ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_PRED_BAND, ARROW_PRED_BLOCK, ARROW_PROFILE,
                       ARROW_RESCALE, ArrowError)
 
-__all__ = ["ArrowMatrix", "ArrowBatch", "ArrowServer", "ArrowError", "dtype_code", "ARROW_F32", "ARROW_BF16", "ARROW_F16"]
+__all__ = ["ArrowMatrix", "ArrowBatch", "count_tiles", "ArrowServer", "ArrowError", "dtype_code", "ARROW_F32", "ARROW_BF16", "ARROW_F16"]
 
 _DTYPE_NAMES = {"f32": ARROW_F32, "float32": ARROW_F32, "bf16": ARROW_BF16, "bfloat16": ARROW_BF16,
                 "f16": ARROW_F16, "float16": ARROW_F16}
@@ -44,6 +44,25 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _csr(A):
+    """(arrow_csr, arrays that must stay alive while it is used) for a host CSR object."""
+    rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+    colidx = np.ascontiguousarray(A.colidx, dtype=np.int32)
+    values = np.ascontiguousarray(A.values, dtype=np.float64)
+    csr = _native.ArrowCsr(int(A.n), int(rowptr[-1]) if rowptr.size else 0, rowptr.ctypes.data,
+                           colidx.ctypes.data if colidx.size else None,
+                           values.ctypes.data if values.size else None)
+    return csr, (rowptr, colidx, values)
+
+
+def count_tiles(A, b: int) -> int:
+    """``arrow_count_tiles``: distinct non-zero b x b tiles of A in its own order."""
+    csr, _keep = _csr(A)
+    t = ctypes.c_int64()
+    _native.check(_native.lib().arrow_count_tiles(ctypes.byref(csr), int(b), ctypes.byref(t)))
+    return int(t.value)
+
+
 class ArrowMatrix:
     """A decomposed matrix: ``arrow_decompose`` on construction, ``arrow_free`` on close.
 
@@ -56,12 +75,7 @@ class ArrowMatrix:
                  segment: int = 0, device: int = -1):
         L = _native.lib()
         self._h = ctypes.c_void_p()
-        rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int64)
-        colidx = np.ascontiguousarray(A.colidx, dtype=np.int32)
-        values = np.ascontiguousarray(A.values, dtype=np.float64)
-        csr = _native.ArrowCsr(int(A.n), int(rowptr[-1]) if rowptr.size else 0, rowptr.ctypes.data,
-                               colidx.ctypes.data if colidx.size else None,
-                               values.ctypes.data if values.size else None)
+        csr, _keep = _csr(A)
         o = _native.ArrowOpts()
         _native.check(L.arrow_opts_default(ctypes.byref(o)))
         o.seed = seed
@@ -153,6 +167,22 @@ class ArrowMatrix:
         _native.check(_native.lib().arrow_level_csr(self._h, i, rowptr.ctypes.data, colidx.ctypes.data,
                                                     vals.ctypes.data))
         return rowptr, colidx[:nz], vals[:nz]
+
+    def level_shape(self, i: int) -> dict:
+        """``arrow_get_level_shape``: n_active, nnz, head_nnz, band_nnz and non-zero tiles of B_i."""
+        sh = _native.ArrowLevelShape()
+        _native.check(_native.lib().arrow_get_level_shape(self._h, int(i), ctypes.byref(sh)))
+        return {f: int(getattr(sh, f)) for f, _ in sh._fields_}
+
+    def structure_report(self) -> dict:
+        """Every level's shape plus the totals: the order l, the non-zero tiles summed over the
+        levels, and each level's share of the entries and of the rows."""
+        levels = [self.level_shape(i) for i in range(self.num_levels)]
+        for lv in levels:
+            lv["nnz_share"] = lv["nnz"] / max(1, self.nnz)
+            lv["row_share"] = lv["n_active"] / max(1, self.n)
+        return {"n": self.n, "nnz": self.nnz, "b": self.b, "levels": levels,
+                "tiles": sum(lv["tiles"] for lv in levels)}
 
     def status(self) -> int:
         """Read and clear the device status word (raises ArrowError on a timed-out wait)."""

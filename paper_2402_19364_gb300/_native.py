@@ -48,6 +48,11 @@ class ArrowStats(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("decompose_seconds", ctypes.c_double)]
 
 
+class ArrowLevelShape(ctypes.Structure):
+    _fields_ = [("n_active", ctypes.c_int64), ("nnz", ctypes.c_int64), ("head_nnz", ctypes.c_int64),
+                ("band_nnz", ctypes.c_int64), ("tiles", ctypes.c_int64)]
+
+
 class ArrowTuning(ctypes.Structure):
     _fields_ = [("tile_rows", ctypes.c_int32), ("tile_nnz", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("carveout", ctypes.c_int32)]
@@ -97,6 +102,8 @@ SIGNATURES = {
     "arrow_level_info": (_I32, [_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "arrow_level_perm": (_I32, [_P, _I32, _P]),
     "arrow_level_csr": (_I32, [_P, _I32, _P, _P, _P]),
+    "arrow_get_level_shape": (_I32, [_P, _I32, ctypes.POINTER(ArrowLevelShape)]),
+    "arrow_count_tiles": (_I32, [ctypes.POINTER(ArrowCsr), _I64, ctypes.POINTER(_I64)]),
     "arrow_get_stats": (_I32, [_P, ctypes.POINTER(ArrowStats)]),
     "arrow_profile_get": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "arrow_status": (_I32, [_P, ctypes.POINTER(_I32)]),

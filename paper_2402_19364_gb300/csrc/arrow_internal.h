@@ -107,4 +107,9 @@ void build_tiles(arrow_handle_s* h, int tile_rows, int tile_nnz);
 // Serialisation of the host state (decompose.cpp).
 int save_host(const arrow_handle_s* h, const char* path);
 int load_host(arrow_handle_s* h, const char* path);
+// Structure report (decompose.cpp): entries in the head rows/columns, the rest (the band),
+// and the distinct non-zero b x b tiles, of level `level` or of an undecomposed matrix.
+struct ShapeCount { int64_t head = 0, band = 0, tiles = 0; };
+ShapeCount level_shape_host(const arrow_handle_s* h, int level);
+int count_tiles_host(const arrow_csr* A, int64_t b, int64_t* tiles);
 }  // namespace arrow

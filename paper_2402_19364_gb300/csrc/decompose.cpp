@@ -636,6 +636,73 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
     return ARROW_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Structure report: where the entries of a level sit under the tiling of Section 3.1
+// (head rows and columns, the band, the non-zero b x b tiles), and the non-zero tiles of
+// an undecomposed matrix in its own order (the equally sized blocks a 1.5D distribution
+// would deal out, which Section 6 compares against the decomposition's).
+// ---------------------------------------------------------------------------------------
+namespace {
+
+// row_entries(p, emit) calls emit(q) for every entry (p, q) of position row p.  Tile rows
+// are split over threads; a tile row's column tiles are sorted and counted once each.
+template <class RowEntries>
+ShapeCount shape_scan(int64_t n, int64_t b, int threads, RowEntries&& row_entries) {
+    ShapeCount total;
+    if (n <= 0) return total;
+    const int64_t ntr = (n + b - 1) / b;
+    const int T = int(std::max<int64_t>(1, std::min<int64_t>(threads, ntr)));
+    std::vector<ShapeCount> part(T);
+    auto work = [&](int t) {
+        ShapeCount c;
+        std::vector<int64_t> qs;
+        for (int64_t P = ntr * t / T; P < ntr * (t + 1) / T; ++P) {
+            qs.clear();
+            const int64_t p1 = std::min(n, P * b + b);
+            for (int64_t p = P * b; p < p1; ++p)
+                row_entries(p, [&](int64_t q) {
+                    if (p < b || q < b) ++c.head; else ++c.band;
+                    qs.push_back(q / b);
+                });
+            std::sort(qs.begin(), qs.end());
+            c.tiles += int64_t(std::unique(qs.begin(), qs.end()) - qs.begin());
+        }
+        part[t] = c;
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < T; ++t) th.emplace_back(work, t);
+    work(0);
+    for (auto& x : th) x.join();
+    for (const ShapeCount& c : part) { total.head += c.head; total.band += c.band; total.tiles += c.tiles; }
+    return total;
+}
+
+int report_threads() { return int(std::min(256u, std::max(1u, std::thread::hardware_concurrency()))); }
+
+}  // namespace
+
+ShapeCount level_shape_host(const arrow_handle_s* h, int level) {
+    const int64_t n = h->n, b = h->b;
+    const std::vector<int32_t>& perm = h->levels[level].perm;
+    std::vector<int32_t> iperm(n);
+    for (int64_t v = 0; v < n; ++v) iperm[perm[v]] = int32_t(v);
+    return shape_scan(n, b, report_threads(), [&](int64_t p, auto&& emit) {
+        const int64_t v = iperm[p];
+        for (int64_t j = h->rowptr[v]; j < h->rowptr[v + 1]; ++j)
+            if (h->entry_level[j] == level) emit(int64_t(perm[h->colidx[j]]));
+    });
+}
+
+int count_tiles_host(const arrow_csr* A, int64_t b, int64_t* tiles) {
+    if (b < 1) { set_error("arrow_count_tiles: b must be >= 1"); return ARROW_EINVAL; }
+    int rc = validate(A);
+    if (rc != ARROW_OK) return rc;
+    *tiles = shape_scan(A->n, b, report_threads(), [&](int64_t r, auto&& emit) {
+        for (int64_t j = A->rowptr[r]; j < A->rowptr[r + 1]; ++j) emit(int64_t(A->colidx[j]));
+    }).tiles;
+    return ARROW_OK;
+}
+
 }  // namespace arrow
 
 // ---------------------------------------------------------------------------------------

@@ -48,6 +48,9 @@ def _parity(arrow, A, b, seed=0, **kw):
         assert np.array_equal(ci, lv.colidx)
         assert np.array_equal(vv, lv.values)
         assert M.level_info(i) == (lv.n_active, lv.nnz)
+        sh = M.level_shape(i)
+        assert (sh["head_nnz"], sh["band_nnz"], sh["tiles"]) == D.level_shape(lv)
+        assert (sh["n_active"], sh["nnz"]) == (lv.n_active, lv.nnz)
     return M
 
 
@@ -142,6 +145,30 @@ def test_band_predicate_matches_oracle(arrow):
     for i, lv in enumerate(L):
         assert np.array_equal(M.level_perm(i), lv.perm)
         assert M.level_info(i) == (lv.n_active, lv.nnz)
+        sh = M.level_shape(i)
+        assert (sh["head_nnz"], sh["band_nnz"], sh["tiles"]) == D.level_shape(lv)
+
+
+def test_count_tiles_and_structure_report(arrow):
+    cases = [(w.grid2d_64(), 64), (w.grid_stencil((13, 13), seed=2), 13), (w.rmat_gcn(10, 16, seed=5), 32),
+             (w.random_csr(300, 0.02, 3), 7), (w.grid3d(12), 144)]
+    for A, b in cases:
+        for bb in (b, 1, 5, A.n, 10 * A.n):
+            assert arrow.count_tiles(A, bb) == D.count_tiles(A, bb)
+    assert arrow.count_tiles(w.grid_stencil((13, 13), seed=2), 13) == 3 * 13 - 2
+    A = w.grid2d_64()
+    M = arrow.ArrowMatrix(A, 64, host_only=True)
+    rep = M.structure_report()
+    assert len(rep["levels"]) == M.num_levels
+    assert sum(lv["nnz"] for lv in rep["levels"]) == A.nnz
+    assert rep["tiles"] == sum(D.level_shape(lv)[2] for lv in D.la_decompose(A, 64))
+    with pytest.raises(arrow.ArrowError):
+        arrow.count_tiles(A, 0)
+    with pytest.raises(arrow.ArrowError):
+        M.level_shape(M.num_levels)
+    bad = w.Csr(A.n, A.rowptr, A.colidx[::-1].copy(), A.values)          # columns not increasing
+    with pytest.raises(arrow.ArrowError):
+        arrow.count_tiles(bad, 8)
 
 
 def test_fused_program_stats(arrow):

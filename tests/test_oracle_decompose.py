@@ -279,3 +279,50 @@ def test_head_vertices_leave_no_entries():
 def test_b_below_two_rejected():
     with pytest.raises(ValueError):
         D.la_decompose(w.grid2d_64(), 1)
+
+
+def test_fig3_shape_of_b0_and_b1():
+    # Fig. 3 colours B_0's edges: dashed blue = pruned head part, green = band.  Under the
+    # band predicate with pi_0 = identity and b = 2: 4 head edges and 3 band edges, each
+    # stored twice (symmetric), and the b x b tiles they touch, counted by hand:
+    # {0,1}->(0,0); {0,4},{0,5}->(0,2),(2,0); {1,3}->(0,1),(1,0); {2,3}->(1,1);
+    # {3,4}->(1,2),(2,1); {5,6}->(2,3),(3,2)  = 10 tiles.
+    n, b, edges = _fig3()
+    A = _csr_from_edges(n, list(edges))
+    rows = np.repeat(np.arange(n), np.diff(A.rowptr))
+    (rp, ci, vv), n_act, take = D.split_step(n, rows, A.colidx.astype(np.int64), A.values, np.arange(n), b,
+                                             D.pred_band)
+    head = sum(2 for k in edges.values() if k == "head")
+    band = sum(2 for k in edges.values() if k == "band")
+    assert (head, band) == (8, 6)
+    assert D.arrow_shape(np.repeat(np.arange(n), np.diff(rp)), ci, b) == (head, band, 10)
+    # B_1: the remaining edge {2, 5} moved to head positions 0 and 1: one tile, all head
+    lv = D.la_decompose(_csr_from_edges(7, [(2, 5)]), b=2)
+    assert D.level_shape(lv[0]) == (2, 0, 1)
+
+
+def test_count_tiles_closed_forms():
+    # 2D N x N 5-point stencil in natural order, b = N: tile row R holds grid rows R-1, R,
+    # R+1 -> 3N - 2 non-zero tiles; one tile when b = N^2
+    for N in (8, 13):
+        A = w.grid_stencil((N, N), seed=1)
+        assert D.count_tiles(A, N) == 3 * N - 2
+        assert D.count_tiles(A, N * N) == 1
+    # diagonal only, n = 10, b = 3: ceil(10/3) = 4 diagonal tiles; positions 0..2 are head
+    n = 10
+    A = w.Csr(n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n))
+    assert D.count_tiles(A, 3) == 4
+    assert D.arrow_shape(np.arange(n), np.arange(n), 3) == (3, 7, 4)
+
+
+def test_level_shapes_partition_the_entries():
+    A = w.rmat_gcn(9, 8, seed=2)
+    for pred in (D.pred_block, D.pred_band):
+        lv = D.la_decompose(A, b=24, predicate=pred)
+        for L in lv:
+            h, bd, t = D.level_shape(L)
+            assert h + bd == L.nnz and t >= 1
+            # every B_i entry outside the head lies in a diagonal tile (block) or the band
+            rows = np.repeat(np.arange(L.n), np.diff(L.rowptr))
+            off = (rows >= L.b) & (L.colidx >= L.b)
+            assert np.all(pred(rows[off], L.colidx[off], L.b))
