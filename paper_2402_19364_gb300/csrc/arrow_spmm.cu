@@ -1118,22 +1118,6 @@ int arrow_level_perm(arrow_handle h, int32_t i, int32_t* perm_out) {
     return ARROW_OK;
 }
 
-int arrow_get_level_shape(arrow_handle h, int32_t i, arrow_level_shape* out) {
-    if (!h || !out || i < 0 || i >= int32_t(h->levels.size())) { set_error("arrow_get_level_shape: bad argument"); return ARROW_EINVAL; }
-    const ShapeCount c = level_shape_host(h, i);
-    out->n_active = h->levels[i].n_active;
-    out->nnz = h->levels[i].nnz;
-    out->head_nnz = c.head;
-    out->band_nnz = c.band;
-    out->tiles = c.tiles;
-    return ARROW_OK;
-}
-
-int arrow_count_tiles(const arrow_csr* A, int64_t b, int64_t* tiles) {
-    if (!tiles) { set_error("arrow_count_tiles: tiles is NULL"); return ARROW_EINVAL; }
-    return count_tiles_host(A, b, tiles);
-}
-
 int arrow_level_csr(arrow_handle h, int32_t i, int64_t* rowptr, int32_t* colidx, double* vals) {
     if (!h || !rowptr || i < 0 || i >= int32_t(h->levels.size())) { set_error("arrow_level_csr: bad argument"); return ARROW_EINVAL; }
     const int64_t n = h->n;

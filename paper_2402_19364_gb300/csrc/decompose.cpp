@@ -844,3 +844,29 @@ int load_host(arrow_handle_s* h, const char* path) {
 }
 
 }  // namespace arrow
+
+// ---------------------------------------------------------------------------------------
+// C-ABI of the structure report (host only)
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+int arrow_get_level_shape(arrow_handle h, int32_t i, arrow_level_shape* out) {
+    if (!h || !out || i < 0 || i >= int32_t(h->levels.size())) {
+        arrow::set_error("arrow_get_level_shape: bad argument");
+        return ARROW_EINVAL;
+    }
+    const arrow::ShapeCount c = arrow::level_shape_host(h, i);
+    out->n_active = h->levels[i].n_active;
+    out->nnz = h->levels[i].nnz;
+    out->head_nnz = c.head;
+    out->band_nnz = c.band;
+    out->tiles = c.tiles;
+    return ARROW_OK;
+}
+
+int arrow_count_tiles(const arrow_csr* A, int64_t b, int64_t* tiles) {
+    if (!tiles) { arrow::set_error("arrow_count_tiles: tiles is NULL"); return ARROW_EINVAL; }
+    return arrow::count_tiles_host(A, b, tiles);
+}
+
+}  // extern "C"
