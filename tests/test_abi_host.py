@@ -222,3 +222,16 @@ def test_tuning_retiles_and_validates(arrow):
         with pytest.raises(arrow.ArrowError):
             M.set_tuning(*bad)
     assert M.tuning["tile_rows"] == 128                      # unchanged after rejected values
+
+
+def test_structure_report_cli(arrow, capsys):
+    from paper_2402_19364_gb300 import report
+    report.main(["--workload", "grid2d", "--size", "24", "--b", "24", "--predicate", "both"])
+    import json
+    out = json.loads(capsys.readouterr().out)
+    A = w.grid_stencil((24, 24), seed=3)
+    assert out["n"] == A.n and out["nnz"] == A.nnz and len(out["reports"]) == 2
+    for r, pred in zip(out["reports"], (D.pred_block, D.pred_band)):
+        L = D.la_decompose(A, 24, seed=3, predicate=pred)
+        assert [(lv["head_nnz"], lv["band_nnz"], lv["tiles"]) for lv in r["levels"]] == [D.level_shape(x) for x in L]
+        assert r["tiles_input_order"] == D.count_tiles(A, 24) == 3 * 24 - 2
