@@ -654,10 +654,13 @@ def main():
             if spec["rescale"]:
                 e0.record(stream)
                 for _ in range(reps):
-                    # column norms: squares summed over row blocks first (torch's direct dim-0
-                    # reduction of a tall, narrow tensor is slow), then over the blocks
-                    blk = next((d for d in (1024, 1000, 512, 500, 256, 128, 64) if A.n % d == 0), 1)
-                    sq = (Yc * Yc).view(-1, blk, Yc.shape[1]).sum(dim=1).sum(dim=0)
+                    # column norms: the squares viewed as a wide (n/m, m*k) matrix so that the
+                    # dim-0 reduction has m*k outputs to spread over the GPU (torch reduces a
+                    # tall n x 16 tensor over dim 0 at a small fraction of HBM speed), then the
+                    # m partial sums of each column
+                    kk = Yc.shape[1]
+                    m = next((d for d in (64, 32, 16, 8, 4, 2) if A.n % d == 0), 1)
+                    sq = (Yc * Yc).view(-1, m * kk).sum(dim=0).view(m, kk).sum(dim=0)
                     Zc = Yc / torch.sqrt(sq)
                 e1.record(stream)
                 torch.cuda.synchronize()
