@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "arena.h"
 #include "arrow_internal.h"
 #include "batch_kernels.cuh"
 
@@ -29,43 +30,6 @@ namespace {
 
 size_t xsize(int dt) { return dt == ARROW_F32 ? 4 : 2; }
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// First-fit allocator over one device arena with coalescing of neighbouring free blocks.
-struct Arena {
-    size_t cap = 0, in_use = 0, peak = 0;
-    std::map<size_t, size_t> free_;   // offset -> size
-    void init(size_t c) { cap = c; free_.clear(); free_[0] = c; in_use = peak = 0; }
-    bool alloc(size_t bytes, size_t* off) {
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < bytes) continue;
-            *off = it->first;
-            const size_t rest = it->second - bytes;
-            const size_t at = it->first + bytes;
-            free_.erase(it);
-            if (rest) free_[at] = rest;
-            in_use += bytes;
-            peak = std::max(peak, in_use);
-            return true;
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        in_use -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-};
 
 struct Request {
     int64_t id;
