@@ -55,6 +55,13 @@ def _csr(A):
     return csr, (rowptr, colidx, values)
 
 
+def _check_open(mats, what: str) -> None:
+    """The C side holds raw handle pointers: refuse to run on a matrix that was closed."""
+    for m in mats:
+        if not (getattr(m, "_h", None) and m._h.value):
+            raise ArrowError(_native.ARROW_ESTATE, f"{what}: a matrix it uses was closed")
+
+
 def count_tiles(A, b: int) -> int:
     """``arrow_count_tiles``: distinct non-zero b x b tiles of A in its own order."""
     csr, _keep = _csr(A)
@@ -304,6 +311,7 @@ class ArrowBatch:
         xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Xs])
         yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in outs])
         ks = (ctypes.c_int64 * n)(*[x.shape[1] for x in Xs])
+        _check_open(self.mats, "arrow_batch_spmm")
         _native.check(_native.lib().arrow_batch_spmm(self._b, xp, yp, ks, int(iters), xd.pop(),
                                                      ARROW_GRAPH if graph else 0, _stream_ptr(stream)))
         return outs
@@ -324,6 +332,7 @@ class ArrowBatch:
         ks = (ctypes.c_int64 * n)(*[x.shape[1] for x in Xs])
         t = _native.ArrowTuning()
         ms = ctypes.c_double()
+        _check_open(self.mats, "arrow_batch_autotune")
         _native.check(_native.lib().arrow_batch_autotune(self._b, xp, yp, ks, int(iters), dtype_code(Xs[0].dtype),
                                                          _stream_ptr(stream), ctypes.byref(t), ctypes.byref(ms)))
         return {f: getattr(t, f) for f, _ in t._fields_}, ms.value

@@ -235,3 +235,15 @@ def test_structure_report_cli(arrow, capsys):
         L = D.la_decompose(A, 24, seed=3, predicate=pred)
         assert [(lv["head_nnz"], lv["band_nnz"], lv["tiles"]) for lv in r["levels"]] == [D.level_shape(x) for x in L]
         assert r["tiles_input_order"] == D.count_tiles(A, 24) == 3 * 24 - 2
+
+
+def test_closed_matrix_guard(arrow):
+    # batches hold raw handle pointers: the binding refuses a batch call once a member is closed
+    A = w.grid2d_64()
+    Ms = [arrow.ArrowMatrix(A, 64, host_only=True) for _ in range(2)]
+    arrow._check_open(Ms, "test")
+    Ms[1].close()
+    with pytest.raises(arrow.ArrowError) as ei:
+        arrow._check_open(Ms, "arrow_batch_spmm")
+    assert ei.value.code == -5
+    Ms[0].close()
