@@ -252,12 +252,14 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
     forest.assign(std::min<int64_t>(n, int64_t(eu.size())), {0, 0});
     std::atomic<int64_t> fcount{0};
     const uint64_t NONE = ~uint64_t(0);
+    std::vector<int32_t> ecu(eu.size()), ecv(eu.size());   // components of the edge ends this round
     int round = 0;
     while (!eu.empty()) {
         const int64_t m = int64_t(eu.size());
         pfor(m, [&](int64_t b, int64_t e, int) {
             for (int64_t i = b; i < e; ++i) {
                 int32_t cu = comp[eu[i]], cv = comp[ev[i]];
+                ecu[i] = cu; ecv[i] = cv;
                 astore(best[cu], NONE); astore(best[cv], NONE);
                 astore(link[cu], cu); astore(link[cv], cv);
                 astore(stamp[cu], round); astore(stamp[cv], round);
@@ -265,7 +267,7 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
         });
         pfor(m, [&](int64_t b, int64_t e, int) {
             for (int64_t i = b; i < e; ++i) {
-                int32_t cu = comp[eu[i]], cv = comp[ev[i]];
+                int32_t cu = ecu[i], cv = ecv[i];
                 if (cu == cv) continue;
                 atomic_min_relaxed(best[cu], ew[i]);
                 atomic_min_relaxed(best[cv], ew[i]);
@@ -275,7 +277,7 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
         pfor(m, [&](int64_t b, int64_t e, int) {
             int64_t sel = 0;
             for (int64_t i = b; i < e; ++i) {
-                int32_t cu = comp[eu[i]], cv = comp[ev[i]];
+                int32_t cu = ecu[i], cv = ecv[i];
                 if (cu == cv) continue;
                 bool a = aload(best[cu]) == ew[i], c = aload(best[cv]) == ew[i];
                 if (!a && !c) continue;
@@ -290,7 +292,7 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
         // mutual choices form 2-cycles: the smaller label becomes the root
         pfor(m, [&](int64_t b, int64_t e, int) {
             for (int64_t i = b; i < e; ++i) {
-                for (int32_t c : {comp[eu[i]], comp[ev[i]]}) {
+                for (int32_t c : {ecu[i], ecv[i]}) {
                     int32_t l = aload(link[c]);
                     if (l != c && aload(link[l]) == c && c < l) astore(link[c], c);
                 }
@@ -299,7 +301,7 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
         // pointer jumping to the roots
         pfor(m, [&](int64_t b, int64_t e, int) {
             for (int64_t i = b; i < e; ++i) {
-                for (int32_t c : {comp[eu[i]], comp[ev[i]]}) {
+                for (int32_t c : {ecu[i], ecv[i]}) {
                     for (;;) {
                         int32_t l = aload(link[c]);
                         int32_t ll = aload(link[l]);
@@ -346,14 +348,14 @@ void arrange(int64_t n, const std::vector<int32_t>& head, const std::vector<uint
     for (int64_t p = 0; p < hb; ++p) { perm[head[p]] = int32_t(p); iperm[p] = head[p]; }
 
     // tree sizes and smallest ids, keyed by representative
+    // (one pass in vertex order: the first vertex seen of a tree is its smallest id; a
+    // parallel form with atomics contended on the single counter of a spanning tree)
     std::vector<int32_t> tsize(n, 0), tmin(n, INT32_MAX);
-    pfor(n, [&](int64_t b, int64_t e, int) {
-        for (int64_t v = b; v < e; ++v) {
-            if (is_head[v]) continue;
-            std::atomic_ref<int32_t>(tsize[comp[v]]).fetch_add(1, std::memory_order_relaxed);
-            atomic_min_relaxed(tmin[comp[v]], int32_t(v));
-        }
-    });
+    for (int64_t v = 0; v < n; ++v) {
+        if (is_head[v]) continue;
+        const int32_t c = comp[v];
+        if (tsize[c]++ == 0) tmin[c] = int32_t(v);
+    }
     struct Tree { int32_t size, root; int64_t start; };
     std::vector<Tree> multi;
     for (int64_t v = 0; v < n; ++v)
