@@ -119,6 +119,19 @@ def test_invalid_inputs_rejected(arrow):
     assert "strictly increasing" in _bad(arrow, w.Csr(3, np.array([0, 2, 2, 2]), np.array([1, 1], np.int32),
                                                       np.ones(2)), 2).args[0]
     assert _bad(arrow, A, 8, max_levels=1).code == _native.ARROW_EINVAL      # level cap
+    # size limits of the int32 indices: n and nnz below 2^31, checked before any array is read
+    import ctypes
+    L = _native.lib()
+    o = _native.ArrowOpts()
+    L.arrow_opts_default(ctypes.byref(o))
+    o.flags = _native.ARROW_HOST_ONLY
+    h = ctypes.c_void_p()
+    for n, nnz in ((1 << 31, 0), (4, 1 << 31), (-1, 0), (4, -1)):
+        csr = _native.ArrowCsr(n, nnz, None, None, None)
+        assert L.arrow_decompose(ctypes.byref(csr), 8, ctypes.byref(o), ctypes.byref(h)) == _native.ARROW_EINVAL
+        assert not h.value
+        t = ctypes.c_int64()
+        assert L.arrow_count_tiles(ctypes.byref(csr), 8, ctypes.byref(t)) == _native.ARROW_EINVAL
 
 
 def test_state_errors_without_gpu(arrow):
