@@ -316,6 +316,34 @@ typedef struct {
 /* Errors: ARROW_EINVAL (NULL argument, level out of range). */
 int arrow_get_level_shape(arrow_handle h, int32_t i, arrow_level_shape* out);
 
+/* The fused row program the device kernels run (host copy; read-only views that stay valid
+ * until the handle is freed, re-tuned or reloaded).  Rows are pi_0 positions.  Every level's
+ * entries of the vertex at position p sit in row p, in level order and, inside a level, in
+ * increasing level position of the column (the write-back of Alg. 2 with destinations fixed
+ * at preprocessing, Thm. 5.2); each entry names the pi_0 position of the X row it reads (the
+ * level shuffle of Alg. 2 folded into the index) and the index of its value in A.  Rows with
+ * more than long_row entries are split: their short range is empty and their entries sit in
+ * the long stream, cut into segments of at most `segment` entries (Alg. 1's head-row
+ * reduction in two fixed-order stages).  Tiles cut the short rows into the units the rows
+ * kernel stages into shared memory.  Exported for tests and reports. */
+typedef struct {
+    int64_t n, n_short, n_long_entries, n_long_rows, n_segments, n_tiles;
+    int32_t long_row;
+    const int32_t* rowptr;      /* [n+1] short rows */
+    const int32_t* col;         /* [n_short] pi_0 position read */
+    const int32_t* src;         /* [n_short] index of the entry in A */
+    const int32_t* lcol;        /* [n_long_entries] */
+    const int32_t* lsrc;        /* [n_long_entries] */
+    const int32_t* long_rows;   /* [n_long_rows] split rows, ascending */
+    const int32_t* long_segptr; /* [n_long_rows+1] first segment of each split row */
+    const int32_t* seg_begin;   /* [n_segments] entry range of each segment in the long stream */
+    const int32_t* seg_end;     /* [n_segments] */
+    const int32_t* tile_row;    /* [n_tiles+1] first row of each tile */
+    const int32_t* tile_ent;    /* [n_tiles+1] first short entry of each tile */
+} arrow_program;
+/* Errors: ARROW_EINVAL (NULL argument), ARROW_ESTATE (band-predicate handle: no program). */
+int arrow_get_program(arrow_handle h, arrow_program* out);
+
 /* Number of distinct non-zero b x b tiles of A in its own row and column order: the equally
  * sized blocks a 1.5D distribution deals out, against which Section 6 counts the non-zero
  * blocks of the decomposition.  A as for arrow_decompose (host CSR, read only); b >= 1.

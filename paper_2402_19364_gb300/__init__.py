@@ -181,6 +181,20 @@ class ArrowMatrix:
         _native.check(_native.lib().arrow_get_level_shape(self._h, int(i), ctypes.byref(sh)))
         return {f: int(getattr(sh, f)) for f, _ in sh._fields_}
 
+    def program(self) -> dict:
+        """``arrow_get_program``: copies of the fused row program the kernels run (numpy int32)."""
+        pg = _native.ArrowProgram()
+        _native.check(_native.lib().arrow_get_program(self._h, ctypes.byref(pg)))
+        sizes = {"rowptr": pg.n + 1, "col": pg.n_short, "src": pg.n_short, "lcol": pg.n_long_entries,
+                 "lsrc": pg.n_long_entries, "long_rows": pg.n_long_rows, "long_segptr": pg.n_long_rows + 1,
+                 "seg_begin": pg.n_segments, "seg_end": pg.n_segments, "tile_row": pg.n_tiles + 1,
+                 "tile_ent": pg.n_tiles + 1}
+        out = {"long_row": int(pg.long_row)}
+        for f, cnt in sizes.items():
+            ptr = getattr(pg, f)
+            out[f] = np.ctypeslib.as_array(ptr, shape=(int(cnt),)).copy() if cnt > 0 and ptr else np.zeros(0, np.int32)
+        return out
+
     def structure_report(self) -> dict:
         """Every level's shape plus the totals: the order l, the non-zero tiles summed over the
         levels, and each level's share of the entries and of the rows."""

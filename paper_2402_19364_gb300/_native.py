@@ -53,6 +53,14 @@ class ArrowLevelShape(ctypes.Structure):
                 ("band_nnz", ctypes.c_int64), ("tiles", ctypes.c_int64)]
 
 
+class ArrowProgram(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_short", ctypes.c_int64), ("n_long_entries", ctypes.c_int64),
+                ("n_long_rows", ctypes.c_int64), ("n_segments", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
+                ("long_row", ctypes.c_int32)] + [(f, ctypes.POINTER(ctypes.c_int32)) for f in (
+                    "rowptr", "col", "src", "lcol", "lsrc", "long_rows", "long_segptr", "seg_begin", "seg_end",
+                    "tile_row", "tile_ent")]
+
+
 class ArrowTuning(ctypes.Structure):
     _fields_ = [("tile_rows", ctypes.c_int32), ("tile_nnz", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("carveout", ctypes.c_int32)]
@@ -104,6 +112,7 @@ SIGNATURES = {
     "arrow_level_csr": (_I32, [_P, _I32, _P, _P, _P]),
     "arrow_get_level_shape": (_I32, [_P, _I32, ctypes.POINTER(ArrowLevelShape)]),
     "arrow_count_tiles": (_I32, [ctypes.POINTER(ArrowCsr), _I64, ctypes.POINTER(_I64)]),
+    "arrow_get_program": (_I32, [_P, ctypes.POINTER(ArrowProgram)]),
     "arrow_get_stats": (_I32, [_P, ctypes.POINTER(ArrowStats)]),
     "arrow_profile_get": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "arrow_status": (_I32, [_P, ctypes.POINTER(_I32)]),

@@ -866,6 +866,33 @@ int arrow_get_level_shape(arrow_handle h, int32_t i, arrow_level_shape* out) {
     return ARROW_OK;
 }
 
+int arrow_get_program(arrow_handle h, arrow_program* out) {
+    if (!h || !out) { arrow::set_error("arrow_get_program: NULL argument"); return ARROW_EINVAL; }
+    if (h->f_rowptr.empty() && h->n > 0) {
+        arrow::set_error("arrow_get_program: band-predicate handles have no device program");
+        return ARROW_ESTATE;
+    }
+    out->n = h->n;
+    out->n_short = int64_t(h->f_col.size());
+    out->n_long_entries = int64_t(h->l_col.size());
+    out->n_long_rows = int64_t(h->long_rows.size());
+    out->n_segments = int64_t(h->seg_begin.size());
+    out->n_tiles = h->tile_row.empty() ? 0 : int64_t(h->tile_row.size()) - 1;
+    out->long_row = h->long_row;
+    out->rowptr = h->f_rowptr.data();
+    out->col = h->f_col.data();
+    out->src = h->f_src.data();
+    out->lcol = h->l_col.data();
+    out->lsrc = h->l_src.data();
+    out->long_rows = h->long_rows.data();
+    out->long_segptr = h->long_segptr.data();
+    out->seg_begin = h->seg_begin.data();
+    out->seg_end = h->seg_end.data();
+    out->tile_row = h->tile_row.data();
+    out->tile_ent = h->tile_ent.data();
+    return ARROW_OK;
+}
+
 int arrow_count_tiles(const arrow_csr* A, int64_t b, int64_t* tiles) {
     if (!tiles) { arrow::set_error("arrow_count_tiles: tiles is NULL"); return ARROW_EINVAL; }
     return arrow::count_tiles_host(A, b, tiles);
