@@ -27,7 +27,9 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
+#include <new>
 #include <numeric>
 #include <thread>
 #include <utility>
@@ -449,8 +451,18 @@ void build_tiles(arrow_handle_s* h, int tile_rows, int tile_nnz) {
     h->tune.tile_nnz = tile_nnz;
 }
 
+// Host fault injection for the tests of the allocation-failure path: with the environment
+// variable ARROW_INJECT_HOST_ALLOC_FAILURE=k the decomposition throws std::bad_alloc as it
+// starts level k, as a failed allocation there would (arrow_decompose turns it into
+// ARROW_ENOMEM and frees the partial handle).  Unset in normal use.
+static int injected_alloc_failure_level() {
+    const char* s = std::getenv("ARROW_INJECT_HOST_ALLOC_FAILURE");
+    return s && *s ? std::atoi(s) : -1;
+}
+
 int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow_opts& o) {
     auto t0 = std::chrono::steady_clock::now();
+    const int fail_level = injected_alloc_failure_level();
     g_threads = o.nthreads > 0 ? o.nthreads : int(std::max(1u, std::thread::hardware_concurrency()));
     g_threads = std::min(g_threads, 256);
     if (b < 2) { set_error("arrow_decompose: b must be >= 2 (Section 4.1)"); return ARROW_EINVAL; }
@@ -486,6 +498,7 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
     std::vector<uint8_t> is_head(n), touched(n);
     int level = 0;
     while (!act.empty()) {
+        if (level == fail_level) throw std::bad_alloc();
         if (level >= max_levels) {
             set_error("arrow_decompose: more than max_levels levels");
             return ARROW_EINVAL;

@@ -260,3 +260,21 @@ def test_closed_matrix_guard(arrow):
         arrow._check_open(Ms, "arrow_batch_spmm")
     assert ei.value.code == -5
     Ms[0].close()
+
+
+def test_injected_host_allocation_failure(arrow, monkeypatch):
+    # a failed host allocation in the middle of LA-Decompose surfaces as ARROW_ENOMEM with no
+    # handle returned, and the next decomposition is unaffected
+    from paper_2402_19364_gb300 import _native
+    A = w.grid2d_64()
+    for level in (0, 1, 2):
+        monkeypatch.setenv("ARROW_INJECT_HOST_ALLOC_FAILURE", str(level))
+        for _ in range(20):
+            with pytest.raises(arrow.ArrowError) as ei:
+                arrow.ArrowMatrix(A, 64, host_only=True)
+            assert ei.value.code == _native.ARROW_ENOMEM and "allocation" in str(ei.value)
+    monkeypatch.setenv("ARROW_INJECT_HOST_ALLOC_FAILURE", "99")     # past the last level: no failure
+    M = arrow.ArrowMatrix(A, 64, host_only=True)
+    monkeypatch.delenv("ARROW_INJECT_HOST_ALLOC_FAILURE")
+    ref = D.la_decompose(A, 64)
+    assert M.num_levels == len(ref) and np.array_equal(M.level_perm(0), ref[0].perm)
