@@ -250,12 +250,11 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
     std::iota(comp.begin(), comp.end(), 0);
     std::vector<uint64_t> best(n);
     std::vector<int32_t> link(n);
-    std::vector<int32_t> stamp(n, -1);
+    std::iota(link.begin(), link.end(), 0);
     forest.assign(std::min<int64_t>(n, int64_t(eu.size())), {0, 0});
     std::atomic<int64_t> fcount{0};
     const uint64_t NONE = ~uint64_t(0);
     std::vector<int32_t> ecu(eu.size()), ecv(eu.size());   // components of the edge ends this round
-    int round = 0;
     while (!eu.empty()) {
         const int64_t m = int64_t(eu.size());
         pfor(m, [&](int64_t b, int64_t e, int) {
@@ -264,7 +263,6 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
                 ecu[i] = cu; ecv[i] = cv;
                 astore(best[cu], NONE); astore(best[cv], NONE);
                 astore(link[cu], cu); astore(link[cv], cv);
-                astore(stamp[cu], round); astore(stamp[cv], round);
             }
         });
         pfor(m, [&](int64_t b, int64_t e, int) {
@@ -313,14 +311,12 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
                 }
             }
         });
-        pfor(n, [&](int64_t b, int64_t e, int) {
-            for (int64_t v = b; v < e; ++v) {
-                int32_t c = comp[v];
-                if (stamp[c] == round) {
-                    int32_t r = c;
-                    for (;;) { int32_t l = link[r]; if (l == r) break; r = l; }
-                    comp[v] = r;
-                }
+        // the edge ends take their component's new root (one step after the jumping); the
+        // other vertices follow their links once, after the last round
+        pfor(m, [&](int64_t b, int64_t e, int) {
+            for (int64_t i = b; i < e; ++i) {
+                astore(comp[eu[i]], aload(link[ecu[i]]));
+                astore(comp[ev[i]], aload(link[ecv[i]]));
             }
         });
         // drop edges inside one component
@@ -334,8 +330,16 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
             for (int64_t j = b; j < e; ++j) { nu[j] = eu[keep_idx[j]]; nv[j] = ev[keep_idx[j]]; nw[j] = ew[keep_idx[j]]; }
         });
         eu.swap(nu); ev.swap(nv); ew.swap(nw);
-        ++round;
     }
+    // every vertex to its tree's representative: a component's link, once it stopped being a
+    // root, points at the root that absorbed it, so the chains end at the final roots
+    pfor(n, [&](int64_t b, int64_t e, int) {
+        for (int64_t v = b; v < e; ++v) {
+            int32_t r = comp[v];
+            for (;;) { const int32_t l = link[r]; if (l == r) break; r = l; }
+            comp[v] = r;
+        }
+    });
     forest.resize(fcount.load());
 }
 
