@@ -364,28 +364,73 @@ void arrange(int64_t n, const std::vector<int32_t>& head, const std::vector<uint
     }
     struct Tree { int32_t size, root; int64_t start; };
     std::vector<Tree> multi;
-    for (int64_t v = 0; v < n; ++v)
-        if (!is_head[v] && comp[v] == v && tsize[v] >= 2) multi.push_back({tsize[v], tmin[v], 0});
+    pfilter(n, multi, [&](int64_t v) { return !is_head[v] && comp[v] == v && tsize[v] >= 2; },
+            [&](int64_t v) { return Tree{tsize[v], tmin[v], 0}; });
     std::sort(multi.begin(), multi.end(), [](const Tree& x, const Tree& y) {
         return x.size != y.size ? x.size > y.size : x.root < y.root;
     });
     int64_t pos = hb;
     for (auto& t : multi) { t.start = pos; pos += t.size; }
-    // single vertices: those holding an entry first, each group in id order
-    for (int pass = 0; pass < 2; ++pass)
-        for (int64_t v = 0; v < n; ++v)
-            if (!is_head[v] && tsize[comp[v]] == 1 && (touched[v] != 0) == (pass == 0)) {
-                perm[v] = int32_t(pos); iperm[pos] = int32_t(v); ++pos;
-            }
+    // single vertices: those holding an entry first, each group in id order (per-chunk counts,
+    // then every chunk writes its own consecutive positions)
+    {
+        auto single = [&](int64_t v) { return !is_head[v] && tsize[comp[v]] == 1; };
+        std::vector<int64_t> c0(g_threads + 1, 0), c1(g_threads + 1, 0);
+        pfor(n, [&](int64_t b, int64_t e, int t) {
+            int64_t a = 0, z = 0;
+            for (int64_t v = b; v < e; ++v)
+                if (single(v)) ++(touched[v] ? a : z);
+            c0[t + 1] = a;
+            c1[t + 1] = z;
+        });
+        for (int t = 0; t < g_threads; ++t) { c0[t + 1] += c0[t]; c1[t + 1] += c1[t]; }
+        const int64_t p0 = pos, p1 = pos + c0[g_threads];
+        pfor(n, [&](int64_t b, int64_t e, int t) {
+            int64_t a = p0 + c0[t], z = p1 + c1[t];
+            for (int64_t v = b; v < e; ++v)
+                if (single(v)) {
+                    int64_t& q = touched[v] ? a : z;
+                    perm[v] = int32_t(q);
+                    iperm[q] = int32_t(v);
+                    ++q;
+                }
+        });
+        pos = p1 + c1[g_threads];
+    }
 
-    // forest adjacency
+    // forest adjacency (the order inside a vertex's list does not matter: the tree, its
+    // subtree sizes and the sorted child order it yields are the same)
     std::vector<int64_t> fptr(n + 1, 0);
-    for (auto& e : forest) { fptr[e.first + 1]++; fptr[e.second + 1]++; }
-    for (int64_t v = 0; v < n; ++v) fptr[v + 1] += fptr[v];
+    const int64_t nf = int64_t(forest.size());
+    pfor(nf, [&](int64_t b, int64_t e, int) {
+        for (int64_t i = b; i < e; ++i) {
+            std::atomic_ref<int64_t>(fptr[forest[i].first + 1]).fetch_add(1, std::memory_order_relaxed);
+            std::atomic_ref<int64_t>(fptr[forest[i].second + 1]).fetch_add(1, std::memory_order_relaxed);
+        }
+    });
+    {
+        std::vector<int64_t> part(g_threads + 1, 0);
+        pfor(n, [&](int64_t b, int64_t e, int t) {
+            int64_t sum = 0;
+            for (int64_t v = b; v < e; ++v) sum += fptr[v + 1];
+            part[t + 1] = sum;
+        });
+        for (int t = 0; t < g_threads; ++t) part[t + 1] += part[t];
+        pfor(n, [&](int64_t b, int64_t e, int t) {
+            int64_t run = part[t];
+            for (int64_t v = b; v < e; ++v) { run += fptr[v + 1]; fptr[v + 1] = run; }
+        });
+    }
     std::vector<int32_t> fadj(fptr[n]);
     {
         std::vector<int64_t> fill(fptr.begin(), fptr.end() - 1);
-        for (auto& e : forest) { fadj[fill[e.first]++] = e.second; fadj[fill[e.second]++] = e.first; }
+        pfor(nf, [&](int64_t b, int64_t e, int) {
+            for (int64_t i = b; i < e; ++i) {
+                const int32_t u = forest[i].first, v = forest[i].second;
+                fadj[std::atomic_ref<int64_t>(fill[u]).fetch_add(1, std::memory_order_relaxed)] = v;
+                fadj[std::atomic_ref<int64_t>(fill[v]).fetch_add(1, std::memory_order_relaxed)] = u;
+            }
+        });
     }
     std::vector<int32_t> parent(n, -1), sub(n, 0);
     std::atomic<int64_t> next{0};
