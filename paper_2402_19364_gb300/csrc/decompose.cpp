@@ -432,41 +432,52 @@ void arrange(int64_t n, const std::vector<int32_t>& head, const std::vector<uint
             }
         });
     }
-    std::vector<int32_t> parent(n, -1), sub(n, 0);
+    // Each tree is laid out in its own breadth-first numbering: a vertex's children are
+    // appended together, so they form one contiguous range of that numbering, parents come
+    // before children, and the subtree sizes and positions are computed over small dense
+    // arrays instead of by vertex id (the giant spanning tree of a mesh spans most of n).
     std::atomic<int64_t> next{0};
     auto worker = [&] {
-        std::vector<int32_t> order;
+        std::vector<int32_t> order, par, kid0, subq;
+        std::vector<int64_t> posq;
         std::vector<int32_t> kids;
         for (;;) {
             int64_t ti = next.fetch_add(1);
             if (ti >= int64_t(multi.size())) return;
             const Tree& t = multi[ti];
-            order.clear();
-            order.push_back(t.root);
-            parent[t.root] = -1;
+            order.assign(1, t.root);
+            par.assign(1, -1);
+            kid0.clear();
             for (size_t q = 0; q < order.size(); ++q) {
-                int32_t v = order[q];
+                const int32_t v = order[q];
+                const int32_t pv = par[q] >= 0 ? order[size_t(par[q])] : -1;
+                kid0.push_back(int32_t(order.size()));
                 for (int64_t j = fptr[v]; j < fptr[v + 1]; ++j) {
-                    int32_t u = fadj[j];
-                    if (u == parent[v]) continue;
-                    parent[u] = v;
+                    const int32_t u = fadj[j];
+                    if (u == pv) continue;
                     order.push_back(u);
+                    par.push_back(int32_t(q));
                 }
             }
-            for (int32_t v : order) sub[v] = 1;
-            for (size_t q = order.size(); q-- > 1;) sub[parent[order[q]]] += sub[order[q]];
-            perm[t.root] = int32_t(t.start);
-            for (int32_t v : order) {
+            const size_t sz = order.size();
+            kid0.push_back(int32_t(sz));
+            subq.assign(sz, 1);
+            for (size_t q = sz; q-- > 1;) subq[size_t(par[q])] += subq[q];
+            posq.assign(sz, 0);
+            posq[0] = t.start;
+            for (size_t q = 0; q < sz; ++q) {
                 kids.clear();
-                for (int64_t j = fptr[v]; j < fptr[v + 1]; ++j)
-                    if (fadj[j] != parent[v]) kids.push_back(fadj[j]);
+                for (int32_t c = kid0[q]; c < kid0[q + 1]; ++c) kids.push_back(c);
                 std::sort(kids.begin(), kids.end(), [&](int32_t x, int32_t y) {
-                    return sub[x] != sub[y] ? sub[x] < sub[y] : x < y;
+                    return subq[x] != subq[y] ? subq[x] < subq[y] : order[x] < order[y];
                 });
-                int64_t run = int64_t(perm[v]) + 1;
-                for (int32_t u : kids) { perm[u] = int32_t(run); run += sub[u]; }
+                int64_t run = posq[q] + 1;
+                for (int32_t c : kids) { posq[c] = run; run += subq[c]; }
             }
-            for (int32_t v : order) iperm[perm[v]] = v;
+            for (size_t q = 0; q < sz; ++q) {
+                perm[order[q]] = int32_t(posq[q]);
+                iperm[posq[q]] = order[q];
+            }
         }
     };
     int T = std::max(1, std::min<int>(g_threads, int(multi.size())));
