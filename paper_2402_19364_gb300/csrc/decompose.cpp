@@ -273,20 +273,25 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
                 atomic_min_relaxed(best[cv], ew[i]);
             }
         });
+        // each chunk keeps its selected edges and appends them in one reservation (one shared
+        // counter per chunk, not per edge: the forest is a set, its order is not used)
         std::atomic<int64_t> selected{0};
         pfor(m, [&](int64_t b, int64_t e, int) {
-            int64_t sel = 0;
+            std::vector<std::pair<int32_t, int32_t>> mine;
             for (int64_t i = b; i < e; ++i) {
                 int32_t cu = ecu[i], cv = ecv[i];
                 if (cu == cv) continue;
                 bool a = aload(best[cu]) == ew[i], c = aload(best[cv]) == ew[i];
                 if (!a && !c) continue;
-                forest[fcount.fetch_add(1, std::memory_order_relaxed)] = {eu[i], ev[i]};
+                mine.push_back({eu[i], ev[i]});
                 if (a) astore(link[cu], cv);
                 if (c) astore(link[cv], cu);
-                ++sel;
             }
-            selected.fetch_add(sel);
+            if (!mine.empty()) {
+                const int64_t at = fcount.fetch_add(int64_t(mine.size()), std::memory_order_relaxed);
+                std::copy(mine.begin(), mine.end(), forest.begin() + at);
+                selected.fetch_add(int64_t(mine.size()));
+            }
         });
         if (selected.load() == 0) break;
         // mutual choices form 2-cycles: the smaller label becomes the root
