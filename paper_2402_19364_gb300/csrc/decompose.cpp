@@ -570,11 +570,20 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
         }
         std::fill(deg.begin(), deg.end(), 0);
         std::fill(touched.begin(), touched.end(), 0);
+        // act stays sorted by row (it is filtered in order), so a chunk counts each row's
+        // off-diagonal entries in one run; only the rows cut by a chunk boundary are shared
         pfor(int64_t(act.size()), [&](int64_t bb, int64_t e, int) {
-            for (int64_t i = bb; i < e; ++i) {
-                astore(touched[act[i].r], uint8_t(1));   // S is symmetric: rows cover columns
-                if (act[i].r != act[i].c)
-                    std::atomic_ref<int32_t>(deg[act[i].r]).fetch_add(1, std::memory_order_relaxed);
+            for (int64_t i = bb; i < e;) {
+                const int32_t r = act[i].r;
+                int32_t cnt = 0;
+                int64_t j = i;
+                for (; j < e && act[j].r == r; ++j) cnt += act[j].c != r;
+                astore(touched[r], uint8_t(1));          // S is symmetric: rows cover columns
+                if (i == bb || j == e)
+                    std::atomic_ref<int32_t>(deg[r]).fetch_add(cnt, std::memory_order_relaxed);
+                else
+                    deg[r] = cnt;
+                i = j;
             }
         });
         std::vector<int32_t> head = select_head(deg, b);
