@@ -58,6 +58,31 @@ void pfor(int64_t n, F&& f) {
     for (auto& x : th) x.join();
 }
 
+// f(row_begin, row_end, thread) over the rows [0, n) in g_threads chunks of about equal
+// entry counts (ptr: entry prefix over the rows, ptr[0] = 0): a power-law matrix keeps most
+// of its entries in a few rows, which row-count chunks would hand to one thread.
+template <class F>
+void pfor_rows(int64_t n, const int64_t* ptr, F&& f) {
+    const int64_t total = n > 0 ? ptr[n] : 0;
+    const int T = g_threads;
+    if (total < 32768 || T <= 1) {
+        if (n > 0) f(int64_t(0), n, 0);
+        return;
+    }
+    std::vector<int64_t> cut(T + 1, 0);
+    cut[T] = n;
+    for (int t = 1; t < T; ++t) {
+        const int64_t target = total * t / T;
+        const int64_t r = int64_t(std::upper_bound(ptr, ptr + n + 1, target) - ptr) - 1;
+        cut[t] = std::min(n, std::max(cut[t - 1], r));
+    }
+    std::vector<std::thread> th;
+    th.reserve(T);
+    for (int t = 0; t < T; ++t)
+        if (cut[t + 1] > cut[t]) th.emplace_back([&f, &cut, t] { f(cut[t], cut[t + 1], t); });
+    for (auto& x : th) x.join();
+}
+
 // Order-preserving parallel filter: out receives emit(i) for every i with keep(i).
 template <class T, class Keep, class Emit>
 void pfilter(int64_t n, std::vector<T>& out, Keep&& keep, Emit&& emit) {
@@ -165,13 +190,30 @@ bool row_has(const int64_t* ptr, const int32_t* col, int64_t r, int32_t c) {
 
 void build_sym(const arrow_csr* A, SymPattern& S) {
     const int64_t n = A->n;
+    // structurally symmetric iff every entry above the diagonal has its mirror below and
+    // both sides hold as many entries (the mirror map is then a bijection); the mirror of
+    // (r, c), c > r, is searched in row c, rarely a hub row when hubs have small ids
+    // (chunks of entries, not of rows: a power-law matrix keeps most entries in a few rows)
     std::atomic<bool> sym{true};
-    pfor(n, [&](int64_t b, int64_t e, int) {
-        for (int64_t r = b; r < e && sym.load(std::memory_order_relaxed); ++r)
-            for (int64_t j = A->rowptr[r]; j < A->rowptr[r + 1]; ++j)
-                if (!row_has(A->rowptr, A->colidx, A->colidx[j], int32_t(r))) { sym.store(false); return; }
+    std::atomic<int64_t> upper{0}, lower{0};
+    pfor(A->nnz, [&](int64_t b, int64_t e, int) {
+        int64_t up = 0, lo = 0;
+        int64_t r = int64_t(std::upper_bound(A->rowptr, A->rowptr + n + 1, b) - A->rowptr) - 1;
+        for (int64_t j = b; j < e; ++j) {
+            while (A->rowptr[r + 1] <= j) ++r;
+            const int32_t c = A->colidx[j];
+            if (c > r) {
+                ++up;
+                if (!row_has(A->rowptr, A->colidx, c, int32_t(r))) { sym.store(false); return; }
+            } else if (c < r) {
+                ++lo;
+            }
+            if ((j & 4095) == 0 && !sym.load(std::memory_order_relaxed)) return;
+        }
+        upper.fetch_add(up);
+        lower.fetch_add(lo);
     });
-    if (sym.load()) {
+    if (sym.load() && upper.load() == lower.load()) {
         S.ptr = A->rowptr;
         S.col = A->colidx;
         S.nnz = A->nnz;
@@ -554,7 +596,7 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
 
     std::vector<uint8_t> lvlS(S.nnz, 255);
     std::vector<Ent> act(S.nnz);
-    pfor(n, [&](int64_t bb, int64_t e, int) {
+    pfor_rows(n, S.ptr, [&](int64_t bb, int64_t e, int) {
         for (int64_t r = bb; r < e; ++r)
             for (int64_t j = S.ptr[r]; j < S.ptr[r + 1]; ++j) act[j] = {int32_t(r), S.col[j], int32_t(j)};
     });
@@ -636,7 +678,7 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
     const int nl = int(h->levels.size());
     std::vector<std::vector<int64_t>> cnt(g_threads, std::vector<int64_t>(nl, 0));
     std::vector<std::vector<int64_t>> mx(g_threads, std::vector<int64_t>(nl, -1));
-    pfor(n, [&](int64_t bb, int64_t e, int t) {
+    pfor_rows(n, A->rowptr, [&](int64_t bb, int64_t e, int t) {
         for (int64_t r = bb; r < e; ++r)
             for (int64_t j = A->rowptr[r]; j < A->rowptr[r + 1]; ++j) {
                 uint8_t l = S.a2s.empty() ? lvlS[j] : lvlS[S.a2s[j]];
@@ -693,7 +735,9 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
         h->l_src.resize(nl_ent);
         std::vector<int32_t> long_index(n, -1);
         for (size_t i = 0; i < h->long_rows.size(); ++i) long_index[h->long_rows[i]] = int32_t(i);
-        pfor(n, [&](int64_t bb, int64_t e, int) {
+        std::vector<int64_t> lenp(n + 1, 0);   // entries of the pi_0 rows, as a prefix (chunking)
+        for (int64_t p = 0; p < n; ++p) lenp[p + 1] = lenp[p] + len[p];
+        pfor_rows(n, lenp.data(), [&](int64_t bb, int64_t e, int) {
             std::vector<std::pair<uint64_t, int32_t>> tmp;
             for (int64_t p = bb; p < e; ++p) {
                 int32_t v = iperm0[p];
