@@ -303,8 +303,13 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
             for (int64_t i = b; i < e; ++i) {
                 int32_t cu = comp[eu[i]], cv = comp[ev[i]];
                 ecu[i] = cu; ecv[i] = cv;
-                astore(best[cu], NONE); astore(best[cv], NONE);
-                astore(link[cu], cu); astore(link[cv], cv);
+                // resets written only where they change something: a large component is the
+                // end of many edges, and unconditional stores would bounce its cache line
+                // between all threads
+                if (aload(best[cu]) != NONE) astore(best[cu], NONE);
+                if (aload(best[cv]) != NONE) astore(best[cv], NONE);
+                if (aload(link[cu]) != cu) astore(link[cu], cu);
+                if (aload(link[cv]) != cv) astore(link[cv], cv);
             }
         });
         pfor(m, [&](int64_t b, int64_t e, int) {
@@ -362,8 +367,9 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
         // other vertices follow their links once, after the last round
         pfor(m, [&](int64_t b, int64_t e, int) {
             for (int64_t i = b; i < e; ++i) {
-                astore(comp[eu[i]], aload(link[ecu[i]]));
-                astore(comp[ev[i]], aload(link[ecv[i]]));
+                const int32_t ru = aload(link[ecu[i]]), rv = aload(link[ecv[i]]);
+                if (aload(comp[eu[i]]) != ru) astore(comp[eu[i]], ru);
+                if (aload(comp[ev[i]]) != rv) astore(comp[ev[i]], rv);
             }
         });
         // drop edges inside one component
