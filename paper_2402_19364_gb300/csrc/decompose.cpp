@@ -29,6 +29,7 @@
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <numeric>
 #include <thread>
@@ -296,12 +297,20 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
     forest.assign(std::min<int64_t>(n, int64_t(eu.size())), {0, 0});
     std::atomic<int64_t> fcount{0};
     const uint64_t NONE = ~uint64_t(0);
-    std::vector<int32_t> ecu(eu.size()), ecv(eu.size());   // components of the edge ends this round
-    while (!eu.empty()) {
-        const int64_t m = int64_t(eu.size());
+    // the round's edges live in (U, Vv, W)[0, m); the filter moves the survivors to the other
+    // buffer of each pair (allocated once, never zero-filled: it is written before it is read)
+    const int64_t m0 = int64_t(eu.size());
+    std::unique_ptr<int32_t[]> su(new int32_t[size_t(std::max<int64_t>(1, m0))]);
+    std::unique_ptr<int32_t[]> sv(new int32_t[size_t(std::max<int64_t>(1, m0))]);
+    std::unique_ptr<uint64_t[]> sw(new uint64_t[size_t(std::max<int64_t>(1, m0))]);
+    int32_t *U = eu.data(), *Vv = ev.data(), *U2 = su.get(), *V2 = sv.get();
+    uint64_t *W = ew.data(), *W2 = sw.get();
+    std::vector<int32_t> ecu(static_cast<size_t>(m0)), ecv(static_cast<size_t>(m0));   // edge ends' components this round
+    int64_t m = m0;
+    while (m > 0) {
         pfor(m, [&](int64_t b, int64_t e, int) {
             for (int64_t i = b; i < e; ++i) {
-                int32_t cu = comp[eu[i]], cv = comp[ev[i]];
+                int32_t cu = comp[U[i]], cv = comp[Vv[i]];
                 ecu[i] = cu; ecv[i] = cv;
                 // resets written only where they change something: a large component is the
                 // end of many edges, and unconditional stores would bounce its cache line
@@ -316,8 +325,8 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
             for (int64_t i = b; i < e; ++i) {
                 int32_t cu = ecu[i], cv = ecv[i];
                 if (cu == cv) continue;
-                atomic_min_relaxed(best[cu], ew[i]);
-                atomic_min_relaxed(best[cv], ew[i]);
+                atomic_min_relaxed(best[cu], W[i]);
+                atomic_min_relaxed(best[cv], W[i]);
             }
         });
         // each chunk keeps its selected edges and appends them in one reservation (one shared
@@ -328,9 +337,9 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
             for (int64_t i = b; i < e; ++i) {
                 int32_t cu = ecu[i], cv = ecv[i];
                 if (cu == cv) continue;
-                bool a = aload(best[cu]) == ew[i], c = aload(best[cv]) == ew[i];
+                bool a = aload(best[cu]) == W[i], c = aload(best[cv]) == W[i];
                 if (!a && !c) continue;
-                mine.push_back({eu[i], ev[i]});
+                mine.push_back({U[i], Vv[i]});
                 if (a) astore(link[cu], cv);
                 if (c) astore(link[cv], cu);
             }
@@ -368,21 +377,28 @@ void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::v
         pfor(m, [&](int64_t b, int64_t e, int) {
             for (int64_t i = b; i < e; ++i) {
                 const int32_t ru = aload(link[ecu[i]]), rv = aload(link[ecv[i]]);
-                if (aload(comp[eu[i]]) != ru) astore(comp[eu[i]], ru);
-                if (aload(comp[ev[i]]) != rv) astore(comp[ev[i]], rv);
+                if (aload(comp[U[i]]) != ru) astore(comp[U[i]], ru);
+                if (aload(comp[Vv[i]]) != rv) astore(comp[Vv[i]], rv);
             }
         });
-        // drop edges inside one component
-        std::vector<int32_t> nu, nv;
-        std::vector<uint64_t> nw;
-        std::vector<int64_t> keep_idx;
-        pfilter(m, keep_idx, [&](int64_t i) { return comp[eu[i]] != comp[ev[i]]; },
-                [&](int64_t i) { return i; });
-        nu.resize(keep_idx.size()); nv.resize(keep_idx.size()); nw.resize(keep_idx.size());
-        pfor(int64_t(keep_idx.size()), [&](int64_t b, int64_t e, int) {
-            for (int64_t j = b; j < e; ++j) { nu[j] = eu[keep_idx[j]]; nv[j] = ev[keep_idx[j]]; nw[j] = ew[keep_idx[j]]; }
+        // drop edges inside one component (order kept: per-chunk counts, then each chunk
+        // writes its survivors at its offset)
+        std::vector<int64_t> cnt(size_t(g_threads) + 1, 0);
+        pfor(m, [&](int64_t b, int64_t e, int t) {
+            int64_t c = 0;
+            for (int64_t i = b; i < e; ++i) c += comp[U[i]] != comp[Vv[i]];
+            cnt[size_t(t) + 1] = c;
         });
-        eu.swap(nu); ev.swap(nv); ew.swap(nw);
+        for (int t = 0; t < g_threads; ++t) cnt[size_t(t) + 1] += cnt[size_t(t)];
+        pfor(m, [&](int64_t b, int64_t e, int t) {
+            int64_t o = cnt[size_t(t)];
+            for (int64_t i = b; i < e; ++i)
+                if (comp[U[i]] != comp[Vv[i]]) { U2[o] = U[i]; V2[o] = Vv[i]; W2[o] = W[i]; ++o; }
+        });
+        m = cnt[size_t(g_threads)];
+        std::swap(U, U2);
+        std::swap(Vv, V2);
+        std::swap(W, W2);
     }
     // every vertex to its tree's representative: a component's link, once it stopped being a
     // root, points at the root that absorbed it, so the chains end at the final roots
