@@ -42,6 +42,25 @@ namespace {
 
 int g_threads = 1;
 
+// Allocator whose resize leaves trivially constructible elements uninitialised: the large
+// per-level arrays below are always written in full (in parallel) before they are read, and
+// value-initialising them first would be a serial pass over gigabytes.
+template <class T>
+struct DefaultInitAlloc : std::allocator<T> {
+    using value_type = T;
+    DefaultInitAlloc() = default;
+    template <class U>
+    DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
+    template <class U>
+    struct rebind { using other = DefaultInitAlloc<U>; };
+    template <class U>
+    void construct(U* p) noexcept { ::new (static_cast<void*>(p)) U; }
+    template <class U, class... Args>
+    void construct(U* p, Args&&... args) { ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...); }
+};
+template <class T>
+using uvec = std::vector<T, DefaultInitAlloc<T>>;
+
 // f(begin, end, thread) over [0, n) in g_threads contiguous chunks.
 template <class F>
 void pfor(int64_t n, F&& f) {
@@ -85,8 +104,8 @@ void pfor_rows(int64_t n, const int64_t* ptr, F&& f) {
 }
 
 // Order-preserving parallel filter: out receives emit(i) for every i with keep(i).
-template <class T, class Keep, class Emit>
-void pfilter(int64_t n, std::vector<T>& out, Keep&& keep, Emit&& emit) {
+template <class Vec, class Keep, class Emit>
+void pfilter(int64_t n, Vec& out, Keep&& keep, Emit&& emit) {
     int T_ = (n < 32768) ? 1 : g_threads;
     std::vector<int64_t> cnt(T_ + 1, 0);
     auto count = [&](int64_t b, int64_t e, int t) {
@@ -287,7 +306,7 @@ std::vector<int32_t> select_head(const std::vector<int32_t>& deg, int64_t b) {
 // Minimum spanning forest of the edge set (unique keys) by parallel Boruvka.
 // On return comp[v] is the representative of v's tree (every vertex, isolated ones
 // are their own representative) and `forest` holds the forest edges (any order).
-void boruvka(int64_t n, std::vector<int32_t> eu, std::vector<int32_t> ev, std::vector<uint64_t> ew,
+void boruvka(int64_t n, uvec<int32_t> eu, uvec<int32_t> ev, uvec<uint64_t> ew,
              std::vector<int32_t>& comp, std::vector<std::pair<int32_t, int32_t>>& forest) {
     comp.resize(n);
     std::iota(comp.begin(), comp.end(), 0);
@@ -617,7 +636,7 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
     if (S.nnz >= (int64_t(1) << 31)) { set_error("arrow_decompose: symmetric pattern too large"); return ARROW_EINVAL; }
 
     std::vector<uint8_t> lvlS(S.nnz, 255);
-    std::vector<Ent> act(S.nnz);
+    uvec<Ent> act(S.nnz);
     pfor_rows(n, S.ptr, [&](int64_t bb, int64_t e, int) {
         for (int64_t r = bb; r < e; ++r)
             for (int64_t j = S.ptr[r]; j < S.ptr[r + 1]; ++j) act[j] = {int32_t(r), S.col[j], int32_t(j)};
@@ -656,10 +675,10 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
 
         // edges of G_i' = G_i[V \ V^h], keyed by the level's random weights
         const uint64_t salt = splitmix64(o.seed + uint64_t(level));
-        std::vector<int32_t> eu, ev;
-        std::vector<uint64_t> ew;
+        uvec<int32_t> eu, ev;
+        uvec<uint64_t> ew;
         {
-            std::vector<int64_t> idx;
+            uvec<int64_t> idx;
             pfilter(int64_t(act.size()), idx,
                     [&](int64_t i) { const Ent& x = act[i]; return x.r < x.c && !is_head[x.r] && !is_head[x.c]; },
                     [&](int64_t i) { return i; });
@@ -681,7 +700,7 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
 
         // steps 3-4: entries inside the arrow shape go to B_i, the rest stays
         const int32_t* perm = L.perm.data();
-        std::vector<Ent> rest;
+        uvec<Ent> rest;
         pfilter(int64_t(act.size()), rest,
                 [&](int64_t i) {
                     const Ent& x = act[i];
@@ -982,7 +1001,8 @@ int load_host(arrow_handle_s* h, const char* path) {
         return ARROW_EINVAL;
     }
     // structural consistency of what the device path will index
-    bool bad = int64_t(h->rowptr.size()) != n + 1 || int64_t(h->f_rowptr.size()) != (n ? n + 1 : h->f_rowptr.size()) ||
+    bool bad = int64_t(h->rowptr.size()) != n + 1 ||
+               int64_t(h->f_rowptr.size()) != (n ? n + 1 : int64_t(h->f_rowptr.size())) ||
                h->f_col.size() != h->f_src.size() || h->l_col.size() != h->l_src.size() ||
                h->seg_begin.size() != h->seg_end.size() || h->tile_row.size() != h->tile_ent.size();
     for (const Level& l : h->levels) bad = bad || int64_t(l.perm.size()) != n;
