@@ -280,10 +280,23 @@ void build_sym(const arrow_csr* A, SymPattern& S) {
 std::vector<int32_t> select_head(const std::vector<int32_t>& deg, int64_t b) {
     const int64_t n = int64_t(deg.size());
     const int64_t hb = std::min<int64_t>(b, n);
-    int32_t maxdeg = 0;
-    for (int64_t v = 0; v < n; ++v) maxdeg = std::max(maxdeg, deg[v]);
+    // degree histogram (per-chunk maxima and counts, summed in chunk order)
+    std::vector<int32_t> cmax(size_t(g_threads), 0);
+    pfor(n, [&](int64_t lo, int64_t hi, int t) {
+        int32_t m = 0;
+        for (int64_t v = lo; v < hi; ++v) m = std::max(m, deg[v]);
+        cmax[size_t(t)] = m;
+    });
+    const int32_t maxdeg = *std::max_element(cmax.begin(), cmax.end());
+    std::vector<std::vector<int64_t>> ccnt(static_cast<size_t>(g_threads));
+    pfor(n, [&](int64_t lo, int64_t hi, int t) {
+        std::vector<int64_t>& c = ccnt[size_t(t)];
+        c.assign(size_t(maxdeg) + 2, 0);
+        for (int64_t v = lo; v < hi; ++v) c[size_t(deg[v])]++;
+    });
     std::vector<int64_t> cnt(size_t(maxdeg) + 2, 0);
-    for (int64_t v = 0; v < n; ++v) cnt[deg[v]]++;
+    for (const auto& c : ccnt)
+        for (size_t d = 0; d < c.size(); ++d) cnt[d] += c[d];
     // threshold D: #(deg > D) < hb <= #(deg >= D)
     int64_t above = 0;
     int32_t D = maxdeg;
@@ -292,14 +305,15 @@ std::vector<int32_t> select_head(const std::vector<int32_t>& deg, int64_t b) {
         above += cnt[D];
     }
     std::vector<int32_t> head;
-    head.reserve(hb);
-    for (int64_t v = 0; v < n; ++v)
-        if (deg[v] > D) head.push_back(int32_t(v));
+    pfilter(n, head, [&](int64_t v) { return deg[v] > D; }, [&](int64_t v) { return int32_t(v); });
     std::sort(head.begin(), head.end(), [&](int32_t x, int32_t y) {
         return deg[x] != deg[y] ? deg[x] > deg[y] : x < y;
     });
-    for (int64_t v = 0; v < n && int64_t(head.size()) < hb; ++v)
-        if (deg[v] == D) head.push_back(int32_t(v));
+    if (int64_t(head.size()) < hb) {
+        std::vector<int32_t> tie;   // degree exactly D, in id order
+        pfilter(n, tie, [&](int64_t v) { return deg[v] == D; }, [&](int64_t v) { return int32_t(v); });
+        for (size_t i = 0; i < tie.size() && int64_t(head.size()) < hb; ++i) head.push_back(tie[i]);
+    }
     return head;
 }
 
