@@ -255,6 +255,11 @@ def run_reference(a, spec):
     n_full = {"grid3d": spec["N"] ** 3, "grid2d": spec["N"] ** 2, "rmat": 1 << spec["N"]}[spec["name"]]
     A, desc = make_sample(spec, 8_000_000 if cores > 1 else 4_000_000)
     X = w.features(A.n, spec["k"], seed=spec["seed_x"]).astype(np.float64)
+    try:
+        it(A, X, 1, rescale=spec["rescale"])
+    except Exception:                                  # the C form failed here: time the scipy form
+        from oracle import spmm as S
+        it, cores, what = S.iterate, 1, "scipy FP64 CSR product, one core"
     for _ in range(a.warmup):
         it(A, X, 1, rescale=spec["rescale"])
     t0 = time.perf_counter()
