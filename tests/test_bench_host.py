@@ -63,3 +63,24 @@ def test_peaks_and_job_value():
     # whole-job throughput: every rank's units over the slowest rank's time
     assert bench.job_value(20, 4, 100.0) == pytest.approx(800.0)
     assert bench.max_over_ranks(None, 3.5) == 3.5
+
+
+def test_reference_arm_prints_the_contract_line():
+    # the reference arm times the CPU oracle only: it runs here, without a GPU, and prints one
+    # JSON line with the keys the benchmark contract names
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "grid2d", "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=600,
+                         cwd=bench.ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
