@@ -692,7 +692,25 @@ def main():
                                "ms_column_norm": ms_norm,
                                "what": "torch CSR @ dense (cusparseSpMM), f32, natural vertex order"
                                        + (", + column normalisation (torch reductions)" if spec["rescale"] else "")}
-            del As, crow, col, vals, Xc, Yc
+            del As, Xc, Yc
+            if dt_name != "f32":
+                # the same product with the values and X in the workload's 16-bit type, where
+                # the library takes it (reported beside the FP32 form, not instead of it)
+                try:
+                    As16 = torch.sparse_csr_tensor(crow, col, vals.to(tdt), (A.n, A.n))
+                    for _ in range(3):
+                        Y16 = As16 @ Xd
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    for _ in range(reps):
+                        Y16 = As16 @ Xd
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    out["cusparse"]["ms_spmm_" + dt_name] = e0.elapsed_time(e1) / reps
+                    del As16, Y16
+                except Exception as ex:
+                    out["cusparse"]["ms_spmm_" + dt_name] = f"unavailable: {str(ex)[:120]}"
+            del crow, col, vals
             torch.cuda.empty_cache()
         except Exception as ex:  # comparator only: report, do not fail the bench
             out["cusparse"] = {"error": str(ex)[:200]}
