@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--no-cusparse", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-fp32", action="store_true", help="skip the FP32 arm of a 16-bit workload")
+    p.add_argument("--no-sub", action="store_true", help="default workload only: skip the other configurations' records")
+    p.add_argument("--sub", default="grid2d,rmat,batch,serve", help="which other configurations to attach")
     p.add_argument("--tuning", default="", help="tile_rows,tile_nnz,ctas_per_sm,carveout: fixed rows-kernel tuning "
                    "instead of autotuning (keeps a profiler's launch list short)")
     return p.parse_args()
@@ -221,6 +224,8 @@ def cpu_oracle():
     """(iterate function, host threads it uses, description) of the CPU oracle: the C form of
     the FP64 product over all host cores, or the scipy form on one core if it cannot be built."""
     try:
+        import __graft_entry__
+        __graft_entry__._build_oracle_c()             # compiled by the build step; no-op when current
         from oracle import cspmm as C
         return C.iterate, C.threads(), "C FP64 CSR product (oracle/c), rows over the host cores"
     except Exception:
@@ -472,7 +477,9 @@ def run_serve(a):
         v = np.array(list(lat.values()))
         return {"requests": n, "throughput_rps": n / span, "p50_ms": float(np.percentile(v, 50) * 1e3),
                 "p99_ms": float(np.percentile(v, 99) * 1e3), "mean_ms": float(v.mean() * 1e3),
-                "steps": st["steps"], "peak_state_bytes": st["peak_bytes"]}
+                "steps": st["steps"], "peak_state_bytes": st["peak_bytes"],
+                "host_s_in_step": st["host_seconds"], "wait_s_for_gpu": st["wait_seconds"],
+                "gpu_busy_s": st["gpu_seconds"], "gpu_busy_frac": st["gpu_seconds"] / span, "span_s": span}
 
     warm = make_requests(64)
     run(warm, np.zeros(len(warm)))
@@ -480,6 +487,7 @@ def run_serve(a):
     cap = run(closed, np.zeros(len(closed)))
     C = cap["throughput_rps"]
     results = []
+    stream_08 = None
     for frac in (0.5, 0.8, 0.95):
         reqs = make_requests(count if frac == 0.8 else min(count, 1000))
         arrivals = np.cumsum(rng.exponential(1.0 / (frac * C), count))
@@ -488,7 +496,48 @@ def run_serve(a):
         r["rate_rps"] = frac * C
         r["load"] = frac
         results.append(r)
+        if frac == 0.8:
+            stream_08 = (reqs, arrivals)
     main = results[1]
+
+    # The plain FP32 form on the same requests: one arrow_spmm call per request (FP32 values
+    # and X, one rows launch per iteration), served one at a time in arrival order.  Each
+    # request's device time is measured with CUDA events; the latencies follow from the
+    # arrival times of the 0.8 C stream by FIFO order: finish_i = max(arrival_i,
+    # finish_{i-1}) + service_i.
+    fp32 = None
+    if not a.no_fp32:
+        n32 = min(len(stream_08[0]), 1000)
+        mats32 = [m.copy("f32") for m in mats]
+        x32 = [xin[i].float() for i in range(len(mats))]
+        y32 = [torch.empty(m.n * 128, device="cuda", dtype=torch.float32) for m in mats]
+        stream = torch.cuda.current_stream()
+        for m, k, it in stream_08[0][:8]:                  # warm-up
+            mats32[m].spmm(x32[m][: mats[m].n * k].view(mats[m].n, k), it, out=y32[m][: mats[m].n * k].view(mats[m].n, k))
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n32)]
+        for (m, k, it), (s0, s1) in zip(stream_08[0][:n32], evs):
+            s0.record(stream)
+            mats32[m].spmm(x32[m][: mats[m].n * k].view(mats[m].n, k), it, out=y32[m][: mats[m].n * k].view(mats[m].n, k))
+            s1.record(stream)
+        torch.cuda.synchronize()
+        service = np.array([s0.elapsed_time(s1) / 1e3 for s0, s1 in evs])
+        arr = stream_08[1][:n32]
+        finish = np.empty(n32)
+        t = 0.0
+        for i in range(n32):
+            t = max(arr[i], t) + service[i]
+            finish[i] = t
+        lat = finish - arr
+        fp32 = {"requests": n32, "capacity_rps": n32 / service.sum(), "mean_service_ms": float(service.mean() * 1e3),
+                "at_0.8C": {"rate_rps": 0.8 * C, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                            "throughput_rps": n32 / (finish[-1] - arr[0])},
+                "what": "FP32 values and X, one arrow_spmm call per request, one request at a time (FIFO) on the "
+                        "first requests of the 0.8 C stream; latencies from the measured device times"}
+        for m in mats32:
+            m.close()
+        del x32, y32
     out = {"metric": "arrow-SpMM serving p50/p99 latency and throughput (continuous batching)",
            "value": main["throughput_rps"], "unit": "requests/s", "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
            "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
@@ -497,8 +546,198 @@ def run_serve(a):
                                   "k in {16,32,64,128} BF16, iterations U{5..50}, 64 slots, 64 GiB state budget",
                       "pool": [{"family": info[i][0], "n": info[i][1], "nnz": info[i][2]} for i in range(len(mats))],
                       "prep_s": t_prep},
-           "closed_loop": cap, "by_rate": results}
+           "closed_loop": cap, "by_rate": results, "fp32_per_request": fp32}
     print(json.dumps(out), flush=True)
+
+
+def time_calls(arrow, M, Xd, Yd, iters, rescale, steps, warmup, pg, stream, flush=None):
+    """Warm-up calls, then `steps` timed arrow_spmm calls with CUDA events on the launching
+    stream (barrier + synchronize on both sides, max over ranks).  With `flush` (a buffer
+    larger than L2) the buffer is written between calls and each call is timed on its own.
+    Per-kernel device times come from the library's own events (ARROW_PROFILE)."""
+    import torch
+    for _ in range(warmup):
+        M.spmm(Xd, iters, rescale=rescale, out=Yd)
+    torch.cuda.synchronize()
+    for kind in (arrow.ARROW_K_ROWS, arrow.ARROW_K_SEGMENTS, arrow.ARROW_K_NORM, arrow.ARROW_K_PERMUTE):
+        M.profile_get(kind)
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e0.record(stream)
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(i & 0xff)
+        starts[i].record(stream)
+        M.spmm(Xd, iters, rescale=rescale, out=Yd, profile=True)
+        marks[i].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    step_ms = [starts[i].elapsed_time(marks[i]) for i in range(steps)]
+    ms_total = sum(step_ms) if flush is not None else e0.elapsed_time(e1)
+    ms_total = max_over_ranks(pg, ms_total)
+    km, launches = {}, 0
+    for name, kind in (("rows", arrow.ARROW_K_ROWS), ("segments", arrow.ARROW_K_SEGMENTS),
+                       ("norm", arrow.ARROW_K_NORM), ("permute", arrow.ARROW_K_PERMUTE)):
+        ms, cnt = M.profile_get(kind)
+        km[name] = ms
+        km[name + "_launches"] = cnt
+        launches += cnt
+    return {"ms_total": ms_total, "launches": launches, "kernel_ms": {c: km[c] for c in ("rows", "segments", "norm", "permute")},
+            "rows_launches": km["rows_launches"], "segments_launches": km["segments_launches"],
+            "step_ms": {"mean": sum(step_ms) / len(step_ms), "min": min(step_ms), "max": max(step_ms)}}
+
+
+def roofline_record(M, k, dt_name, tm, spec, peak, peak_kind):
+    """roofline of one iteration's rows + split-row kernels: algorithmic bytes (A's values and
+    indices, row pointers, every level's active X rows once, Y once) over their device time
+    per iteration, against the measured HBM copy bandwidth.  traffic: DRAM bytes of one
+    iteration from the committed ncu summary, when it was taken on this kernel source and
+    this workload (spec None: not looked up)."""
+    ab = M.algorithmic_bytes_per_iter(k, dt_name)
+    per_launch_s = (tm["kernel_ms"]["rows"] + tm["kernel_ms"]["segments"]) / max(1, tm["rows_launches"]) / 1e3
+    achieved = ab["total"] / per_launch_s / 1e9
+    traffic = None
+    tr = kernel_traffic(workload_key(spec)) if spec is not None else None
+    if tr is not None:
+        try:
+            traffic = float(tr["dram_bytes_per_launch_full_size"])
+        except (KeyError, ValueError):
+            traffic = None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind,
+            "kernel": "arrow_rows_kernel" + (" + arrow_segments_kernel + arrow_combine_kernel"
+                                             if tm["segments_launches"] else ""),
+            "algorithmic_bytes_per_launch": ab["total"], "launch_ms": per_launch_s * 1e3,
+            "frac_of_nominal_8000": achieved / 8000.0}
+
+
+def cusparse_record(A, M, Xd, spec, dt_name, stream, reps=5):
+    """cusparseSpMM (the bench-only comparator library, baseline/cusparse_spmm.cu) on the
+    undecomposed matrix: every algorithm (default, CSR_ALG1..3) with row-major and
+    column-major X, in natural vertex order and in the decomposition's first order pi_0, in
+    FP32 and (16-bit workloads) in the workload's type; the best of each type is the
+    comparator.  With the rescale, the column normalisation is timed as one HBM-speed pass
+    (sum of squares, then scale) and added."""
+    import ctypes
+    import torch
+    import __graft_entry__
+    lib = ctypes.CDLL(__graft_entry__._build_cusparse_cmp())
+    lib.cmp_cusparse_spmm.restype = ctypes.c_int
+    lib.cmp_cusparse_spmm.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_float)]
+    lib.cmp_column_normalise.restype = ctypes.c_int
+    lib.cmp_column_normalise.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    dev = Xd.device
+    n, k = A.n, Xd.shape[1]
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    rowptr = torch.from_numpy(A.rowptr).to(dev)
+    col = torch.from_numpy(A.colidx).to(dev).long()
+    val = torch.from_numpy(A.values).to(dev, torch.float32)
+    # pi_0 order: row p = vertex pi_0^{-1}(p), columns renamed by pi_0 and sorted in each row
+    perm = torch.from_numpy(M.level_perm(0)).to(dev).long() if M.num_levels else torch.arange(n, device=dev)
+    row = torch.repeat_interleave(torch.arange(n, device=dev), rowptr[1:] - rowptr[:-1])
+    key = perm[row] * n + perm[col]
+    del row
+    key, order = torch.sort(key)
+    rp_pi = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    rp_pi[1:] = torch.cumsum(torch.bincount(key // n, minlength=n), 0)
+    forms = {"natural": (rowptr.int(), col.int(), val),
+             "pi0": (rp_pi.int(), (key % n).int(), val[order])}
+    del key, order, rp_pi, col
+    types = [("f32", torch.float32, 0)] + ([(dt_name, torch.bfloat16, 1)] if dt_name == "bf16" else [])
+    runs = []
+    best = {}
+    for tname, tdt, tcode in types:
+        Xr = Xd.to(tdt).contiguous()
+        Xc = Xr.t().contiguous()                      # column-major storage of the same n x k matrix
+        Yr = torch.empty_like(Xr)
+        for form, (rp, ci, va) in forms.items():
+            vt = va.to(tdt)
+            for layout, Xb in (("row", Xr), ("col", Xc)):
+                for alg, aname in enumerate(("default", "csr_alg1", "csr_alg2", "csr_alg3")):
+                    ms = ctypes.c_float(0.0)
+                    Yb = Yr if layout == "row" else torch.empty_like(Xc)
+                    rc = lib.cmp_cusparse_spmm(n, A.nnz, rp.data_ptr(), ci.data_ptr(), vt.data_ptr(), tcode,
+                                               Xb.data_ptr(), Yb.data_ptr(), k, tcode, alg, int(layout == "col"), reps,
+                                               sp, ctypes.byref(ms))
+                    r = {"dtype": tname, "order": form, "layout": layout, "alg": aname}
+                    if rc == 0:
+                        r["ms"] = float(ms.value)
+                        if tname not in best or r["ms"] < best[tname]["ms"]:
+                            best[tname] = dict(r)
+                    else:
+                        r["error"] = rc
+                    runs.append(r)
+                    del Yb
+            del vt
+        del Xr, Xc, Yr
+        torch.cuda.synchronize()
+    rec = {"what": "cusparseSpMM (CSR, compute FP32) on the undecomposed matrix; best of algorithm x X layout x "
+                   "vertex order", "best": best, "runs": runs}
+    if "f32" in best:
+        ms_it = best["f32"]["ms"]
+        if spec["rescale"]:
+            # one HBM-speed normalisation pass over the FP32 product (row-major)
+            Y = torch.randn(n, k, device=dev)
+            Z = torch.empty_like(Y)
+            grid = 152 * 8
+            part = torch.empty(grid * k, dtype=torch.float64, device=dev)
+            inv = torch.empty(k, dtype=torch.float32, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for i in range(reps + 2):
+                if i == 2:
+                    e0.record(stream)
+                rc = lib.cmp_column_normalise(Y.data_ptr(), Z.data_ptr(), n, k, part.data_ptr(), grid, inv.data_ptr(), sp)
+                if rc:
+                    raise RuntimeError(f"cmp_column_normalise: {rc}")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_norm = e0.elapsed_time(e1) / reps
+            rec["ms_column_norm"] = ms_norm
+            rec["column_norm_GBps"] = 3 * n * k * 4 / (ms_norm / 1e3) / 1e9
+            ms_it += ms_norm
+            del Y, Z, part, inv
+        rec["ms_per_iter"] = ms_it
+        rec["iters_per_s"] = 1e3 / ms_it
+    return rec
+
+
+# Configurations measured beside the headline in the default run (each in its own process,
+# after the headline's device memory is released): (key, bench arguments).
+SUBRECORDS = [
+    ("grid2d", ["--workload", "grid2d", "--steps", "50", "--warmup", "5"]),
+    ("rmat", ["--workload", "rmat", "--steps", "5", "--warmup", "3"]),
+    ("batch", ["--workload", "batch", "--steps", "5", "--warmup", "3"]),
+    ("serve", ["--workload", "serve"]),
+]
+
+
+def run_subrecords(keys, timeout_s=1800):
+    """Run the other configurations as child processes; their JSON lines, keyed."""
+    recs = {}
+    for key, args in SUBRECORDS:
+        if key not in keys:
+            continue
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), *args], cwd=ROOT, capture_output=True,
+                               text=True, timeout=timeout_s)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            if r.returncode != 0 or not lines:
+                recs[key] = {"error": f"rc={r.returncode}: " + (r.stderr.strip().splitlines() or [""])[-1][:300]}
+            else:
+                recs[key] = json.loads(lines[-1])
+        except Exception as ex:
+            recs[key] = {"error": str(ex)[:300]}
+        recs[key]["wall_s"] = time.perf_counter() - t0
+    return recs
 
 
 def main():
@@ -535,6 +774,10 @@ def main():
     Xd = Xh.cuda()
     Yd = torch.empty_like(Xd)
     stream = torch.cuda.current_stream()
+    # inputs smaller than L2 (the 2D 64x64 latency case) get an L2 flush between timed steps
+    flush = None
+    if Xd.numel() * Xd.element_size() * 2 + A.nnz * 8 < 512 << 20:
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=Xd.device)
 
     t0 = time.perf_counter()
     if fixed_tuning(a):
@@ -543,75 +786,66 @@ def main():
     else:
         tuned, _ = M.autotune(Xd, iters, rescale=spec["rescale"], out=Yd)   # arrow_autotune keeps the fastest
     t_tune = time.perf_counter() - t0
-    for _ in range(max(3, a.warmup)):
-        M.spmm(Xd, iters, rescale=spec["rescale"], out=Yd)
-    torch.cuda.synchronize()
-    M.profile_get(arrow.ARROW_K_ROWS)
 
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    barrier(pg)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    marks = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    e0.record(stream)
-    for i in range(a.steps):
-        M.spmm(Xd, iters, rescale=spec["rescale"], out=Yd, profile=True)
-        marks[i].record(stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(pg)
+    tm = time_calls(arrow, M, Xd, Yd, iters, spec["rescale"], a.steps, max(3, a.warmup), pg, stream, flush)
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    step_ms = [(marks[i - 1] if i else e0).elapsed_time(marks[i]) for i in range(a.steps)]
-    ms_total = max_over_ranks(pg, ms_total)
-    rows_ms, rows_launches = M.profile_get(arrow.ARROW_K_ROWS)
-    seg_ms, seg_launches = M.profile_get(arrow.ARROW_K_SEGMENTS)
-    norm_ms, norm_launches = M.profile_get(arrow.ARROW_K_NORM)
-    perm_ms, perm_launches = M.profile_get(arrow.ARROW_K_PERMUTE)
-    launches = rows_launches + seg_launches + norm_launches + perm_launches
+    ms_total = tm["ms_total"]
     ms_step = ms_total / a.steps
     value = job_value(a.steps * iters, world, ms_total)
-
-    ab = M.algorithmic_bytes_per_iter(k, dt_name)
-    # the rows kernel reads every entry except those of split rows (read by the segment kernel)
     peak, peak_kind = load_peaks()
-    per_launch_s = (rows_ms + seg_ms) / max(1, rows_launches) / 1e3
-    achieved = ab["total"] / per_launch_s / 1e9
-    tr = kernel_traffic(workload_key(spec))
-    traffic = None
-    if tr is not None:
-        try:
-            traffic = float(tr["dram_bytes_per_launch_full_size"])
-        except (KeyError, ValueError):
-            traffic = None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "arrow_rows_kernel" + (" + arrow_segments_kernel" if seg_launches else ""),
-                "algorithmic_bytes_per_launch": ab["total"], "launch_ms": per_launch_s * 1e3,
-                "frac_of_nominal_8000": achieved / 8000.0}
+    roofline = roofline_record(M, k, dt_name, tm, spec, peak, peak_kind)
 
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": a.steps,
-           "warmup": max(3, a.warmup), "ms_per_step": ms_step,
-           "step_ms": {"mean": sum(step_ms) / len(step_ms), "min": min(step_ms), "max": max(step_ms)},
+           "warmup": max(3, a.warmup), "ms_per_step": ms_step, "step_ms": tm["step_ms"],
            "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": dt_name, "data": "synthetic",
            "config": {"workload": spec["desc"], "n": A.n, "nnz": A.nnz, "b": spec["b"], "k": k, "iters": iters,
                       "rescale_fp64": spec["rescale"], "levels": [list(x) for x in levels],
                       "long_rows": st["long_rows"], "segments": st["segments"], "autotuned": tuned,
-                      "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
-           "roofline": roofline, "gpu_launches": launches, "clocks": clk,
-           "kernel_ms": {"rows": rows_ms / a.steps, "segments": seg_ms / a.steps, "norm": norm_ms / a.steps,
-                         "permute": perm_ms / a.steps},
+                      "l2": ("inputs larger than L2 (no flush)" if flush is None else
+                             "inputs smaller than L2: a 512 MiB buffer is written between timed steps, "
+                             "which are timed one by one"),
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roofline, "gpu_launches": tm["launches"], "clocks": clk,
+           "kernel_ms": {c: v / a.steps for c, v in tm["kernel_ms"].items()},
            "prep_s": {"generate": t_gen, "decompose_and_upload": t_dec, "decompose_host": st["decompose_seconds"],
                       "autotune": t_tune}}
+    if spec["name"] == "grid2d":
+        out["us_per_iter"] = ms_step / iters * 1e3
+
+    # ---- the same workload through the FP32 path (values and X in FP32), beside the 16-bit one ----
+    if dt_name != "f32" and not a.no_fp32:
+        M32 = M.copy("f32")
+        X32 = Xd.float()
+        Y32 = torch.empty_like(X32)
+        if fixed_tuning(a):
+            M32.set_tuning(*fixed_tuning(a))
+            tuned32 = M32.tuning
+        else:
+            tuned32, _ = M32.autotune(X32, iters, rescale=spec["rescale"], out=Y32)
+        t32 = time_calls(arrow, M32, X32, Y32, iters, spec["rescale"], a.steps, max(3, a.warmup), pg, stream, flush)
+        M.spmm(Xd, iters, rescale=spec["rescale"], out=Yd)
+        torch.cuda.synchronize()
+        rel = (torch.linalg.vector_norm(Yd.float() - Y32, dim=0) / torch.linalg.vector_norm(Y32, dim=0)).max()
+        out["fp32_arm"] = {"value": job_value(a.steps * iters, world, t32["ms_total"]), "unit": "iters/s",
+                           "ms_per_step": t32["ms_total"] / a.steps, "autotuned": tuned32,
+                           "roofline": roofline_record(M32, k, "f32", t32, None, peak, peak_kind),
+                           "kernel_ms": {c: v / a.steps for c, v in t32["kernel_ms"].items()},
+                           "max_normwise_diff_vs_16bit": float(rel),
+                           "what": "the same decomposition with FP32 values and FP32 X (arrow_handle_copy)"}
+        M32.close()
+        del X32, Y32
+        torch.cuda.empty_cache()
 
     # ---- end to end through the public call, host buffers, copies inside the timed region ----
     # Every step copies its inputs from pinned host memory, runs arrow_spmm_ws and reads its
     # result back.  Two steps are in flight on two streams (each with its own device buffers
     # and workspace), so one step's copies overlap the other's kernels; the one-stream form
     # (copy, compute, copy, nothing overlapped) is reported beside it.
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if not a.no_e2e:
         Xp = Xh.pin_memory()
         Yps = [torch.empty_like(Xp).pin_memory() for _ in range(2)]
@@ -655,65 +889,10 @@ def main():
     # ---- cuSPARSE SpMM on the undecomposed matrix (measured comparison) ----------------------
     if not a.no_cusparse and rank == 0:
         try:
-            crow = torch.from_numpy(A.rowptr.astype(np.int32)).cuda()
-            col = torch.from_numpy(A.colidx).cuda()
-            vals = torch.from_numpy(A.values.astype(np.float32)).cuda().to(tdt if dt_name == "f32" else torch.float32)
-            As = torch.sparse_csr_tensor(crow, col, vals, (A.n, A.n))
-            Xc = Xd.float().clone()
-            Yc = torch.empty_like(Xc)
-            for _ in range(3):
-                Yc = As @ Xc
-            torch.cuda.synchronize()
-            reps = 10
-            e0.record(stream)
-            for _ in range(reps):
-                Yc = As @ Xc
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms_spmm = e0.elapsed_time(e1) / reps
-            ms_norm = 0.0
-            if spec["rescale"]:
-                e0.record(stream)
-                for _ in range(reps):
-                    # column norms: the squares viewed as a wide (n/m, m*k) matrix so that the
-                    # dim-0 reduction has m*k outputs to spread over the GPU (torch reduces a
-                    # tall n x 16 tensor over dim 0 at a small fraction of HBM speed), then the
-                    # m partial sums of each column
-                    kk = Yc.shape[1]
-                    m = next((d for d in (64, 32, 16, 8, 4, 2) if A.n % d == 0), 1)
-                    sq = (Yc * Yc).view(-1, m * kk).sum(dim=0).view(m, kk).sum(dim=0)
-                    Zc = Yc / torch.sqrt(sq)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ms_norm = e0.elapsed_time(e1) / reps
-                del Zc
-            ms_it = ms_spmm + ms_norm
-            out["cusparse"] = {"iters_per_s": 1e3 / ms_it, "ms_per_iter": ms_it, "ms_spmm": ms_spmm,
-                               "ms_column_norm": ms_norm,
-                               "what": "torch CSR @ dense (cusparseSpMM), f32, natural vertex order"
-                                       + (", + column normalisation (torch reductions)" if spec["rescale"] else "")}
-            del As, Xc, Yc
-            if dt_name != "f32":
-                # the same product with the values and X in the workload's 16-bit type, where
-                # the library takes it (reported beside the FP32 form, not instead of it)
-                try:
-                    As16 = torch.sparse_csr_tensor(crow, col, vals.to(tdt), (A.n, A.n))
-                    for _ in range(3):
-                        Y16 = As16 @ Xd
-                    torch.cuda.synchronize()
-                    e0.record(stream)
-                    for _ in range(reps):
-                        Y16 = As16 @ Xd
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    out["cusparse"]["ms_spmm_" + dt_name] = e0.elapsed_time(e1) / reps
-                    del As16, Y16
-                except Exception as ex:
-                    out["cusparse"]["ms_spmm_" + dt_name] = f"unavailable: {str(ex)[:120]}"
-            del crow, col, vals
-            torch.cuda.empty_cache()
+            out["cusparse"] = cusparse_record(A, M, Xd, spec, dt_name, stream)
         except Exception as ex:  # comparator only: report, do not fail the bench
-            out["cusparse"] = {"error": str(ex)[:200]}
+            out["cusparse"] = {"error": str(ex)[:300]}
+        torch.cuda.empty_cache()
 
     # ---- CPU oracle on the host cores (bounded sample) ----------------------------------------
     if not a.no_cpu and rank == 0:
@@ -722,9 +901,15 @@ def main():
         out["cpu_baseline"] = {"value": v, "unit": "iters/s", "cores": cores, "kind": "oracle",
                                "sample": f"2 FP64 iterations ({what}) on {desc} "
                                          f"({rows:,} of {A.n:,} rows), scaled by rows"}
+    M.close()
+    if (spec["name"] == "grid3d" and not a.no_sub and world == 1 and not a.size and not a.k and not a.iters
+            and not a.dtype and not a.tuning):
+        del Xd, Yd, Xh
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        out["configs"] = run_subrecords([x for x in a.sub.split(",") if x])
     if rank == 0:
         print(json.dumps(out), flush=True)
-    M.close()
     if pg is not None:
         pg.destroy_process_group()
 

@@ -71,7 +71,9 @@ typedef struct {
     int32_t  max_levels;  /* cap on the order l of the decomposition; 0 = 254               */
     int32_t  long_row;    /* rows with more entries than this are split; 0 = default (64)   */
     int32_t  segment;     /* entries per split segment; 0 = default (512)                   */
-    int32_t  device;      /* CUDA device ordinal for the upload; -1 = current device        */
+    int32_t  device;      /* CUDA device ordinal for the upload; -1 = current device.  The
+                             caller's current device is restored after the upload; later
+                             calls on the handle need its device current                  */
 } arrow_opts;
 
 /* Fill *o with defaults: seed 0, F32 values, block predicate, upload, all threads. */
@@ -121,8 +123,8 @@ int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t it
  * ARROW_ENOMEM, ARROW_ECUDA (upload).  On error nothing is leaked. */
 int arrow_decompose(const arrow_csr* A, int64_t b, const arrow_opts* o, arrow_handle* out);
 
-/* Upload a handle built with ARROW_HOST_ONLY to the current (or opts.device) GPU.
- * No-op if already uploaded.  Errors: ARROW_EINVAL (band predicate), ARROW_ENOMEM, ARROW_ECUDA. */
+/* Upload a handle built with ARROW_HOST_ONLY to the current (or opts.device) GPU; the
+ * caller's current device is left as it was.  No-op if already uploaded.  Errors: ARROW_EINVAL (band predicate), ARROW_ENOMEM, ARROW_ECUDA. */
 int arrow_upload(arrow_handle h);
 
 /* arrow_handle_copy -- a second handle with the same decomposition (no re-decomposition),
@@ -168,6 +170,7 @@ void arrow_free(arrow_handle h);
  *   flags   : 0, ARROW_RESCALE and/or ARROW_PROFILE.
  *   stream  : cudaStream_t; the call only enqueues work (no host synchronisation), except
  *             that the first call for a given (k, x_dtype) allocates the handle's workspace.
+ * The handle's device must be the current device (ARROW_EINVAL otherwise, nothing launched).
  * Errors: ARROW_EINVAL, ARROW_ESTATE (not uploaded), ARROW_ENOMEM, ARROW_ECUDA. */
 int arrow_spmm(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y,
                int32_t x_dtype, int32_t flags, void* stream);
@@ -182,21 +185,21 @@ int arrow_spmm_ws(arrow_handle h, const void* X, int64_t k, int32_t iters, void*
                   int32_t x_dtype, int32_t flags, void* workspace, size_t ws_bytes, void* stream);
 
 /* arrow_spmm_static -- arrow_spmm for callers that cannot allocate device memory.
- * The paper has no counterpart; it exists for code that must not call cudaMalloc: work
- * recorded while a CUDA graph is being captured (allocation is not allowed then), plugins
- * running inside another framework or inference runtime that owns all device memory, and
- * latency-bound serving loops that forbid allocation after start-up (cudaMalloc/cudaFree
- * synchronise the device).  Same arguments and result as arrow_spmm (X, Y on the device,
- * caller-owned), but the scratch lives in one file-scope device array of 64 MiB that every
- * GPU loading the library holds until the process exits.  Problems whose scratch (two
- * n x k feature buffers, split-row partials, FP64 norm sums: the arrow_workspace_size value)
- * exceeds 64 MiB -- about 500,000 rows at k = 16 in FP32 -- are rejected with ARROW_EINVAL.
- * The call allocates nothing.  The handle's device must be current.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and caches it: make
- * that first call before any stream capture.  All calls share the array and it keeps the
- * last call's contents, so calls whose work overlaps on the GPU (other streams, other
- * threads, other handles) race: serialise them.  ARROW_PROFILE is rejected (it creates
- * events).  Errors: ARROW_EINVAL, ARROW_ESTATE, ARROW_ECUDA. */
+ * The paper has no counterpart; it exists for code that must not call cudaMalloc: plugins
+ * running inside another framework or inference runtime that owns all device memory through
+ * its own allocator, and latency-bound serving loops that forbid allocation after start-up
+ * (cudaMalloc/cudaFree synchronise the device and can stall every stream).  Same arguments
+ * and result as arrow_spmm (X, Y on the device, caller-owned), but the scratch lives in one
+ * file-scope device array of 64 MiB that every GPU loading the library holds until the
+ * process exits.  Problems whose scratch (two n x k feature buffers, split-row partials,
+ * FP64 norm sums: the arrow_workspace_size value) exceeds 64 MiB -- about 500,000 rows at
+ * k = 16 in FP32 -- are rejected with ARROW_EINVAL.  The call allocates nothing.  The
+ * handle's device must be current.  The first call in each CUDA context looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it for that context: make that
+ * first call before any stream capture.  All calls share the array and it keeps the last
+ * call's contents, so calls whose work overlaps on the GPU (other streams, other threads,
+ * other handles) race: serialise them.  ARROW_PROFILE is rejected (it creates events).
+ * Errors: ARROW_EINVAL, ARROW_ESTATE, ARROW_ECUDA. */
 int arrow_spmm_static(arrow_handle h, const void* X, int64_t k, int32_t iters, void* Y,
                       int32_t x_dtype, int32_t flags, void* stream);
 
@@ -222,7 +225,8 @@ int arrow_batch_create(const arrow_handle* handles, int32_t count, arrow_batch* 
  * each.  Results are bit-identical to arrow_spmm on each matrix alone.  flags: 0 or
  * ARROW_GRAPH (capture once, replay while X, Y, k, iters and dtype stay the same).  The call
  * allocates its workspace on first use or growth (outside any capture) and synchronises
- * the stream when X, Y, k or dtype change.  Errors: ARROW_EINVAL, ARROW_ECUDA. */
+ * the stream when X, Y, k or dtype change.  The batch's device must be current (ARROW_EINVAL
+ * otherwise, nothing launched).  Errors: ARROW_EINVAL, ARROW_ECUDA. */
 int arrow_batch_spmm(arrow_batch b, const void* const* X, void* const* Y, const int64_t* k, int32_t iters,
                      int32_t x_dtype, int32_t flags, void* stream);
 
@@ -256,6 +260,9 @@ typedef struct {
     int64_t queued, active, inflight_steps, completed, steps;
     int64_t bytes_in_use, peak_bytes;   /* request state in the budget (peak <= hbm_budget) */
     int32_t status;                     /* device status word (0 = no wait ran out)          */
+    double  host_seconds;   /* time spent in arrow_server_step on the host, without the waits */
+    double  wait_seconds;   /* time arrow_server_step spent waiting for the GPU (max_inflight) */
+    double  gpu_seconds;    /* device time of the retired steps (event before to event after) */
 } arrow_server_stats;
 
 /* Create a server; allocates hbm_budget bytes of device memory and a few pinned staging
@@ -274,6 +281,7 @@ int arrow_server_submit(arrow_server s, arrow_handle h, const void* X, void* Y, 
  * while a slot and budget are free, launch one iteration of every active request (plus the
  * permute-in of new ones and the permute-out of finishing ones) on `stream`, which must be
  * the same for every step.  Waits for the oldest step only when max_inflight steps are queued.
+ * The server's device must be current (ARROW_EINVAL otherwise, nothing launched).
  * *active receives the number of active requests (may be NULL).  Errors: ARROW_EINVAL, ARROW_ECUDA. */
 int arrow_server_step(arrow_server s, void* stream, int32_t* active);
 

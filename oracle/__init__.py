@@ -7,7 +7,7 @@ Plain, slow, obviously correct restatements of what the paper computes:
   its iteration X_{t+1} = sigma(A X_t) (Section 2, "Matrices"), and the
   decomposed product sum_i P_i (B_i (P_i^T X)) of Eq. 1 written out.
 * :mod:`oracle.cspmm` -- the same FP64 product and iteration as a plain C loop
-  (oracle/c/csr_spmm.c, built by :mod:`oracle.build`) whose rows run on all host
+  (oracle/c/csr_spmm.c, compiled by the project's build step) whose rows run on all host
   cores; the timed CPU baseline.
 * :mod:`oracle.decompose` -- LA-Decompose (Section 4.1) with the random
   spanning forest linear arrangement (Section 4.3) and the smallest-first tree

@@ -12,14 +12,20 @@ import ctypes
 
 import numpy as np
 
+import os
+
 _lib = None
+LIB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liboracle_c.so")
 
 
 def lib():
+    """The compiled C loop.  It is compiled (host C compiler, OpenMP when available) by the
+    project's build step, __graft_entry__.build(), which the test session runs first."""
     global _lib
     if _lib is None:
-        from .build import build
-        _lib = ctypes.CDLL(str(build()))
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: run __graft_entry__.build() to compile the oracle's C part")
+        _lib = ctypes.CDLL(LIB)
         _lib.oracle_threads.restype = ctypes.c_int
         _lib.oracle_csr_spmm_f64.restype = None
         _lib.oracle_csr_spmm_f64.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

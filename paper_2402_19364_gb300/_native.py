@@ -74,7 +74,8 @@ class ArrowServerOpts(ctypes.Structure):
 class ArrowServerStats(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int64), ("active", ctypes.c_int64), ("inflight_steps", ctypes.c_int64),
                 ("completed", ctypes.c_int64), ("steps", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64),
-                ("peak_bytes", ctypes.c_int64), ("status", ctypes.c_int32)]
+                ("peak_bytes", ctypes.c_int64), ("status", ctypes.c_int32), ("host_seconds", ctypes.c_double),
+                ("wait_seconds", ctypes.c_double), ("gpu_seconds", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p

@@ -182,6 +182,7 @@ int arrow_batch_spmm(arrow_batch B, const void* const* X, void* const* Y, const 
         set_error("arrow_batch_spmm: feature dtype does not match the values");
         return ARROW_EINVAL;
     }
+    if (int rc0 = require_device(B->device, "arrow_batch_spmm")) return rc0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int V = int(16 / dsize(x_dtype));
     const size_t n_m = B->hs.size();

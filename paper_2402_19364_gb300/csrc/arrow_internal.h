@@ -12,6 +12,17 @@ namespace arrow {
 
 void set_error(const std::string& msg);
 
+// ARROW_OK when `device` is the calling thread's current CUDA device; otherwise ARROW_EINVAL
+// (message names `what`) or ARROW_ECUDA.  Every entry point that launches kernels on a
+// handle's or a server's device pointers checks this first: launched on another GPU they
+// would read memory that GPU does not own.
+int require_device(int device, const char* what);
+
+// Opt a kernel into the large dynamic shared memory and set its shared-memory carveout.
+// Both are attributes of the kernel in the current device's context, so they are cached per
+// (device, kernel) and re-applied when the carveout changes.
+void set_smem_attrs(const void* fn, int carveout);
+
 // Row tiles of the fused row program: by default at most kTileRows rows and kTileNnz entries
 // each (arrow_set_tuning / arrow_autotune change them per handle).  A tile's row pointers and
 // entries are staged into shared memory with bulk copies.

@@ -44,6 +44,7 @@ struct Request {
 };
 
 struct StepRec {
+    cudaEvent_t ev0 = nullptr;                      // recorded before the step's work
     cudaEvent_t ev;
     int stage;
     std::vector<int64_t> ids;                       // requests finished by this step
@@ -80,6 +81,7 @@ struct arrow_server_s {
     std::chrono::steady_clock::time_point epoch = std::chrono::steady_clock::now();
     std::deque<std::pair<int64_t, double>> done;   // (id, latency seconds)
     int64_t next_id = 1, steps = 0, completed = 0;
+    double host_s = 0.0, wait_s = 0.0, gpu_s = 0.0;   // arrow_server_stats' time split
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - epoch).count();
     }
@@ -142,12 +144,17 @@ int retire(arrow_server_s* S, bool block_one) {
         cudaError_t q = cudaEventQuery(r.ev);
         if (q == cudaErrorNotReady) {
             if (!block_one) break;
+            const double w0 = S->now();
             q = cudaEventSynchronize(r.ev);
+            S->wait_s += S->now() - w0;
             block_one = false;
         }
         if (q != cudaSuccess) return cuda_fail(q, "arrow_server_step: step event");
         float ms = 0.f;
         SCK(cudaEventElapsedTime(&ms, S->t0_ev, r.ev));
+        float busy = 0.f;
+        if (r.ev0 && cudaEventElapsedTime(&busy, r.ev0, r.ev) == cudaSuccess) S->gpu_s += double(busy) / 1e3;
+        if (r.ev0) cudaEventDestroy(r.ev0);
         const double t_done = S->t0_host + double(ms) / 1e3;
         for (size_t i = 0; i < r.ids.size(); ++i) S->done.emplace_back(r.ids[i], t_done - r.t_submit[i]);
         S->completed += int64_t(r.ids.size());
@@ -161,7 +168,10 @@ int retire(arrow_server_s* S, bool block_one) {
 
 void server_release(arrow_server_s* S) {
     if (S->stream_set) cudaStreamSynchronize(S->stream);
-    for (auto& r : S->inflight) cudaEventDestroy(r.ev);
+    for (auto& r : S->inflight) {
+        cudaEventDestroy(r.ev);
+        if (r.ev0) cudaEventDestroy(r.ev0);
+    }
     if (S->t0_ev) cudaEventDestroy(S->t0_ev);
     for (char* p : S->stage) cudaFreeHost(p);
     if (S->arena_base) cudaFree(S->arena_base);
@@ -186,8 +196,15 @@ int arrow_server_create(const arrow_server_opts* o, arrow_server* out) {
     arrow_server_s* S = new arrow_server_s();
     S->o = *o;
     if (S->o.max_inflight == 0) S->o.max_inflight = 2;
-    cudaError_t e = cudaSuccess;
-    if (o->device >= 0) e = cudaSetDevice(o->device);
+    // work on o->device, and give the caller back its current device on every return path
+    int prev = -1;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) { delete S; return cuda_fail(e, "arrow_server_create"); }
+    struct Restore {
+        int dev; bool on;
+        ~Restore() { if (on) cudaSetDevice(dev); }
+    } restore{prev, o->device >= 0 && o->device != prev};
+    if (restore.on) e = cudaSetDevice(o->device);
     if (e == cudaSuccess) e = cudaGetDevice(&S->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, S->device);
     if (e == cudaSuccess) e = cudaMalloc(&S->arena_base, size_t(o->hbm_budget));
@@ -254,8 +271,18 @@ int arrow_server_submit(arrow_server S, arrow_handle h, const void* X, void* Y, 
     return ARROW_OK;
 }
 
+static int server_step(arrow_server_s* S, void* stream, int32_t* active_out);
+
 int arrow_server_step(arrow_server S, void* stream, int32_t* active_out) {
     if (!S) { set_error("arrow_server_step: NULL server"); return ARROW_EINVAL; }
+    if (int rc0 = require_device(S->device, "arrow_server_step")) return rc0;
+    const double t0 = S->now(), w0 = S->wait_s;
+    const int rc = server_step(S, stream, active_out);
+    S->host_s += (S->now() - t0) - (S->wait_s - w0);
+    return rc;
+}
+
+static int server_step(arrow_server_s* S, void* stream, int32_t* active_out) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (S->stream_set && s != S->stream) { set_error("arrow_server_step: every step must use the same stream"); return ARROW_EINVAL; }
     if (!S->stream_set) {
@@ -332,6 +359,8 @@ int arrow_server_step(arrow_server S, void* stream, int32_t* active_out) {
             rec.frees.emplace_back(r.off, r.bytes);
         }
     }
+    SCK(cudaEventCreateWithFlags(&rec.ev0, cudaEventDefault));
+    SCK(cudaEventRecord(rec.ev0, s));
     SCK(cudaMemcpyAsync(S->d_desc, desc, size_t(n_m) * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
     // the kernels index the base arrays as [class][n_m + 1]
     for (int c = 0; c < kClasses; ++c)
@@ -399,6 +428,9 @@ int arrow_server_get_stats(arrow_server S, arrow_server_stats* st) {
     int32_t v = 0;
     SCK(cudaMemcpy(&v, S->d_status, sizeof(v), cudaMemcpyDeviceToHost));
     st->status = v;
+    st->host_seconds = S->host_s;
+    st->wait_seconds = S->wait_s;
+    st->gpu_seconds = S->gpu_s;
     return ARROW_OK;
 }
 

@@ -446,6 +446,9 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int cuda_fail(cudaError_t e, const char* what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    // a non-sticky error (a bad device ordinal, a failed allocation) stays recorded as the
+    // thread's last error; clear it so that the next call's launch check does not report it
+    (void)cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? ARROW_ENOMEM : ARROW_ECUDA;
 }
 #define ACK(call)                                      \
@@ -548,9 +551,24 @@ static int upload_values(const arrow_handle_s* h, const std::vector<int32_t>& sr
     return ARROW_OK;
 }
 
+static int upload_to_current(arrow_handle_s* h);
+
+// Upload to opts.device (or the current device); the caller's current device is restored on
+// every return path.
 static int upload_impl(arrow_handle_s* h) {
+    int prev = -1;
+    ACK(cudaGetDevice(&prev));
+    if (h->opts.device >= 0 && h->opts.device != prev) ACK(cudaSetDevice(h->opts.device));
+    const int rc = upload_to_current(h);
+    if (h->opts.device >= 0 && h->opts.device != prev) {
+        cudaError_t e = cudaSetDevice(prev);
+        if (rc == ARROW_OK && e != cudaSuccess) return cuda_fail(e, "arrow_upload: restoring the caller's device");
+    }
+    return rc;
+}
+
+static int upload_to_current(arrow_handle_s* h) {
     DeviceData& d = h->dev;
-    if (h->opts.device >= 0) ACK(cudaSetDevice(h->opts.device));
     ACK(cudaGetDevice(&d.device));
     ACK(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, d.device));
     int rc;
@@ -589,22 +607,38 @@ struct Plan {
     size_t x_bytes, part_bytes, np_bytes, sc_bytes, total;
 };
 
-// Shared-memory opt-in (once per function) and carveout (when it changes) of a kernel.
-static void set_smem_attrs(const void* fn, int carveout) {
+// Shared-memory opt-in and carveout of a kernel, cached per (device, kernel): both are
+// attributes in the current device's context, so a second GPU needs its own opt-in.
+void set_smem_attrs(const void* fn, int carveout) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;   // the launch that follows reports the error
+    struct Seen { int dev; const void* fn; int carveout; };
     static std::mutex mu;
-    static std::vector<std::pair<const void*, int>> seen;
+    static std::vector<Seen> seen;
     std::lock_guard<std::mutex> lock(mu);
     for (auto& e : seen)
-        if (e.first == fn) {
-            if (e.second != carveout) {
+        if (e.dev == dev && e.fn == fn) {
+            if (e.carveout != carveout) {
                 cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
-                e.second = carveout;
+                e.carveout = carveout;
             }
             return;
         }
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
-    seen.emplace_back(fn, carveout);
+    seen.push_back({dev, fn, carveout});
+}
+
+int require_device(int device, const char* what) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (cur != device) {
+        set_error(std::string(what) + ": the current CUDA device (" + std::to_string(cur) +
+                  ") is not the one the data lives on (" + std::to_string(device) + "); make it current first");
+        return ARROW_EINVAL;
+    }
+    return ARROW_OK;
 }
 
 static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags, Plan& p) {
@@ -756,6 +790,7 @@ static int check_spmm_args(const arrow_handle_s* h, const void* X, int64_t k, in
             set_error("arrow_spmm: X and Y must be 16-byte aligned");
             return ARROW_EINVAL;
         }
+        return require_device(h->dev.device, "arrow_spmm");
     }
     return ARROW_OK;
 }
@@ -782,25 +817,66 @@ static int spmm_dispatch(arrow_handle_s* h, const Plan& p, const void* X, int64_
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // 64 MiB
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-static std::mutex g_static_mu;
-static void* g_static_ptr[kMaxDevices] = {};
+// The array's device address is looked up once per CUDA context (a non-primary context on
+// the same GPU, or the primary context re-created after cudaDeviceReset, has its own copy at
+// its own address).  Contexts are told apart by cuCtxGetId, reached through the runtime's
+// driver entry point so that the library does not link libcuda itself.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
 
-// Device address of g_static_scratch on `device` (which must be current), looked up once
-// per device.  In host code the symbol itself is only a host-side stand-in.
-static int static_scratch_ptr(int device, void** out) {
-    if (device < 0 || device >= kMaxDevices) {
-        set_error("arrow_spmm_static: device ordinal out of range");
-        return ARROW_EINVAL;
+static int current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    if (!get_current || !get_id) {
+        set_error("arrow_spmm_static: the driver's context query is unavailable");
+        return ARROW_ECUDA;
     }
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, id) != 0) {
+        set_error("arrow_spmm_static: no current CUDA context");
+        return ARROW_ECUDA;
+    }
+    return ARROW_OK;
+}
+
+static std::mutex g_static_mu;
+static std::vector<std::pair<unsigned long long, void*>> g_static_ptr;   // (context id, address)
+
+// Device address of g_static_scratch in the current context (the handle's device must be
+// current), looked up on the first call in each context.  In host code the symbol itself is
+// only a host-side stand-in, never a device address.
+static int static_scratch_ptr(void** out) {
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[device]) {
-        void* p = nullptr;
+    void* p = nullptr;
+    unsigned long long id = 0;
+    if (current_context_id(&id) != ARROW_OK) {
+        // no context bound to this thread yet: the runtime creates the device's primary
+        // context during the symbol lookup, after which the id can be read
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "arrow_spmm_static: cudaGetSymbolAddress");
-        g_static_ptr[device] = p;
+        int rc = current_context_id(&id);
+        if (rc != ARROW_OK) return rc;
     }
-    *out = g_static_ptr[device];
+    for (auto& c : g_static_ptr)
+        if (c.first == id) { *out = c.second; return ARROW_OK; }
+    if (!p) {
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "arrow_spmm_static: cudaGetSymbolAddress");
+    }
+    g_static_ptr.emplace_back(id, p);
+    *out = p;
     return ARROW_OK;
 }
 
@@ -998,12 +1074,6 @@ int arrow_spmm_static(arrow_handle h, const void* X, int64_t k, int32_t iters, v
         return ARROW_EINVAL;
     }
     if (h->n == 0 || k == 0) return ARROW_OK;
-    int cur = -1;
-    ACK(cudaGetDevice(&cur));
-    if (cur != h->dev.device) {
-        set_error("arrow_spmm_static: make the handle's device current before the call");
-        return ARROW_EINVAL;
-    }
     Plan p;
     if ((rc = make_plan(h, k, x_dtype, flags, p))) return rc;
     if (iters > 0 && p.total > kStaticScratchBytes) {
@@ -1013,10 +1083,11 @@ int arrow_spmm_static(arrow_handle h, const void* X, int64_t k, int32_t iters, v
         return ARROW_EINVAL;
     }
     void* scratch = nullptr;
-    if ((rc = static_scratch_ptr(cur, &scratch))) return rc;
-    // Everything the kernels read from the scratch is written earlier in the same call
-    // (feature buffers, segment partials, norm sums); the norm slots that a smaller grid
-    // leaves unwritten are cleared by the launch code before each step.
+    if ((rc = static_scratch_ptr(&scratch))) return rc;
+    // Everything the kernels read from the scratch is written earlier in the same call: the
+    // feature buffers, the segment partials, and the FP64 norm slots, of which each rows and
+    // combine CTA writes its whole slot (all kc columns of every chunk) every step, so nothing
+    // left by an earlier call is read.
     return spmm_dispatch(h, p, X, k, iters, Y, x_dtype, flags, static_cast<char*>(scratch),
                          static_cast<cudaStream_t>(stream));
 }

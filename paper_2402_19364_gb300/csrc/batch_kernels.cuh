@@ -156,16 +156,11 @@ __global__ void __launch_bounds__(256, kBatchMinBlocks) arrow_batch_rows_kernel(
     if (ps->failed && threadIdx.x == 0) drain_pipeline(ps);
 }
 
-// Opt the batched rows kernel into large dynamic shared memory (once) and set its carveout
-// (when it changes); per instantiation and translation unit.
+// Opt the batched rows kernel into large dynamic shared memory and set its carveout (cached
+// per device and kernel instantiation).
 template <typename TX, typename TV>
 inline void prepare_batch_rows(int carveout) {
-    static int last = -1;
-    if (last == carveout) return;
-    if (last < 0)
-        cudaFuncSetAttribute(arrow_batch_rows_kernel<TX, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(arrow_batch_rows_kernel<TX, TV>, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
-    last = carveout;
+    set_smem_attrs(reinterpret_cast<const void*>(arrow_batch_rows_kernel<TX, TV>), carveout);
 }
 
 // One warp per split-row segment of any matrix (first stage of the head-row reduction): the

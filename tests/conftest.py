@@ -9,3 +9,7 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built library")
     config.addinivalue_line("markers", "slow: long-running (full-size workloads)")
+    # the oracle's C part (the multi-core FP64 product) is compiled by the project's build
+    # step; it is a no-op when the library is up to date
+    import __graft_entry__
+    __graft_entry__._build_oracle_c()

@@ -200,12 +200,50 @@ def test_saved_handle_gives_same_bits(arrow, tmp_path):
     M = arrow.ArrowMatrix(A, 64, long_row=32)
     M.save(tmp_path / "a.arw")
     L = arrow.ArrowMatrix.load(tmp_path / "a.arw")
-    X = torch.from_numpy(w.features(A.n, 32, seed=5)).cuda()
-    assert torch.equal(M.spmm(X, 4), L.spmm(X, 4))
+    Xh = w.features(A.n, 32, seed=5)
+    X = torch.from_numpy(Xh).cuda()
+    YL = L.spmm(X, 4)
+    assert torch.equal(M.spmm(X, 4), YL)
+    # the loaded handle against the oracle, not only against the handle it was saved from
+    R = S.iterate(A, Xh, 4)
+    assert err_inf(YL.cpu().numpy().astype(np.float64), R) <= 1e-5 * 4
     Lb = arrow.ArrowMatrix.load(tmp_path / "a.arw", value_dtype="bf16")
     Yb = Lb.spmm(X.bfloat16(), 4).float()
+    assert err_2(Yb.cpu().numpy().astype(np.float64), R) <= 2e-2
     Yf = M.spmm(X, 4)
     assert float(torch.linalg.vector_norm(Yb - Yf) / torch.linalg.vector_norm(Yf)) < 2e-2
+
+
+def test_device_arguments(arrow):
+    """The upload goes to opts.device and leaves the caller's current device as it was; an
+    ordinal with no GPU is an error and gives no handle; calls on a handle whose device is
+    not current return ARROW_EINVAL and launch nothing (that last part needs two GPUs)."""
+    from paper_2402_19364_gb300 import _native
+    A = w.grid2d_64(seed=1)
+    X = w.features(A.n, 16, seed=2)
+    cur = torch.cuda.current_device()
+    M = arrow.ArrowMatrix(A, 64, device=cur)
+    assert torch.cuda.current_device() == cur
+    Y = M.spmm(torch.from_numpy(X).cuda(), 3).cpu().numpy().astype(np.float64)
+    assert err_inf(Y, S.iterate(A, X, 3)) <= 3e-5
+    with pytest.raises(arrow.ArrowError) as e:
+        arrow.ArrowMatrix(A, 64, device=torch.cuda.device_count())
+    assert e.value.code in (_native.ARROW_ECUDA, _native.ARROW_EINVAL)
+    assert torch.cuda.current_device() == cur
+    if torch.cuda.device_count() < 2:
+        return
+    other = (cur + 1) % torch.cuda.device_count()
+    M1 = arrow.ArrowMatrix(A, 64, device=other)
+    assert torch.cuda.current_device() == cur
+    with torch.cuda.device(other):
+        X1 = torch.from_numpy(X).cuda()
+        Y1 = torch.empty_like(X1)
+    L = _native.lib()
+    for fn in (L.arrow_spmm, L.arrow_spmm_static):
+        rc = fn(M1._h, _native.ctypes.c_void_p(X1.data_ptr()), 16, 2, _native.ctypes.c_void_p(Y1.data_ptr()),
+                _native.ARROW_F32, 0, None)
+        assert rc == _native.ARROW_EINVAL
+        assert b"current" in L.arrow_last_error()
 
 
 # ---- full-size workloads (the launch configuration bench.py times) -----------------------
@@ -215,11 +253,22 @@ def _sample_rows(n, count, seed):
     return np.unique(np.r_[0, n - 1, rng.integers(0, n, count)])
 
 
+def _oracle_columns(A, X, cols, iters, rescale=False):
+    """Every row of the columns `cols` of the oracle's result.  The columns of X_{t+1} =
+    sigma(A X_t) are independent (A acts on each column alone and the rescale divides each
+    column by its own norm), so the multi-core FP64 oracle run on those columns of X gives
+    exactly those columns of the full result."""
+    from oracle import cspmm as C
+    return C.iterate(A, np.ascontiguousarray(X[:, cols], dtype=np.float64), iters, rescale=rescale)
+
+
 def test_full_size_grid3d_400(arrow):
     """3D 400^3 7-point grid (n = 64M, nnz = 447.04M), b = 4096, k = 16 f32, 20 iterations.
 
-    Sampled rows are computed by the oracle one by one (dependency cone of 20 hops);
-    with the rescale on, the column of ones must stay constant and every column has unit norm.
+    Every row of four columns is compared with the multi-core FP64 oracle, with and without
+    the rescale; sampled rows are also computed by the oracle one by one (dependency cone of
+    20 hops); with the rescale on, the column of ones must stay constant and every column has
+    unit norm.
     """
     A = w.grid3d(400, seed=3)
     assert A.n == 64_000_000 and A.nnz == 447_040_000
@@ -242,15 +291,25 @@ def test_full_size_grid3d_400(arrow):
     Yrs = Yr[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
     c = np.sum(Yrs * R, axis=0) / np.sum(R * R, axis=0)
     assert err_inf(Yrs, R * c) <= 1e-5 * 20
+    # every row of four columns against the oracle (FP32 bar: 1e-5 * iters, inf-norm per column)
+    cols = [0, 3, 9, 14]
+    ci = torch.tensor(cols, device="cuda")
+    Yc = Y.index_select(1, ci).cpu().numpy().astype(np.float64)
+    Yrc = Yr.index_select(1, ci).cpu().numpy().astype(np.float64)
+    del Y, Yr
+    assert err_inf(Yc, _oracle_columns(A, X, cols, 20)) <= 1e-5 * 20
+    assert err_inf(Yrc, _oracle_columns(A, X, cols, 20, rescale=True)) <= 1e-5 * 20
 
 
 def test_full_size_rmat23_gcn_bf16(arrow):
     """R-MAT scale 23 (n = 8.39M), symmetrised, self-loops, GCN-normalised; b = 8192; k = 128;
     8 iterations in BF16 storage with FP32 accumulation and in FP32.
 
-    A . d^{1/2} = d^{1/2} holds for the GCN normalisation at any size, so a column set to
-    d^{1/2} must come back unchanged: within 1e-5 * iters (inf-norm, relative) in FP32 and
-    2e-2 (normwise) in BF16; the other columns of the two paths agree normwise within 2e-2.
+    Every row of eight columns (the d^{1/2} column and seven others) is compared with the
+    multi-core FP64 oracle: within 1e-5 * iters (inf-norm, relative) in FP32 and 2e-2
+    (normwise) in BF16.  A . d^{1/2} = d^{1/2} holds for the GCN normalisation at any size, so
+    the column set to d^{1/2} must also come back unchanged; on all 128 columns the two paths
+    agree normwise within 2e-2.
     """
     A = w.rmat_gcn(23, 16, seed=5)
     assert A.n == 1 << 23
@@ -260,8 +319,9 @@ def test_full_size_rmat23_gcn_bf16(arrow):
     X = w.features(A.n, 128, seed=6)
     d = np.sqrt(np.diff(A.rowptr).astype(np.float64))
     X[:, 0] = d
-    del A
+    cols = [0, 1, 17, 42, 63, 64, 101, 127]
     Xf = torch.from_numpy(X).cuda()
+    Xc = np.ascontiguousarray(X[:, cols])
     del X
     iters = 8
     Yf = M32.spmm(Xf, iters)
@@ -271,3 +331,10 @@ def test_full_size_rmat23_gcn_bf16(arrow):
     assert float(torch.linalg.vector_norm(Yb[:, 0].double() - dd) / torch.linalg.vector_norm(dd)) <= 2e-2
     rel = torch.linalg.vector_norm(Yb - Yf, dim=0) / torch.linalg.vector_norm(Yf, dim=0)
     assert float(rel.max()) <= 2e-2
+    ci = torch.tensor(cols, device="cuda")
+    Yfc = Yf.index_select(1, ci).cpu().numpy().astype(np.float64)
+    Ybc = Yb.index_select(1, ci).cpu().numpy().astype(np.float64)
+    del Yf, Yb, Xf
+    R = _oracle_columns(A, Xc, list(range(len(cols))), iters)
+    assert err_inf(Yfc, R) <= 1e-5 * iters
+    assert err_2(Ybc, R) <= 2e-2
