@@ -4,11 +4,16 @@ Eq. 1 (Section 3) states A X = sum_i P_{pi_i} (B_i (P_{pi_i}^T X)): an
 identity, so the arrow-decomposed product reaches exactly (up to rounding
 order) the plain sparse-times-dense product.  That plain product, in FP64, is
 the value oracle.  The iteration X_{t+1} = sigma(A X_t) is the one of
-Section 2 ("Matrices"); the only sigma used here is the per-column L2
-normalisation, reduced in FP64.
+Section 2 ("Matrices").  Section 2 leaves sigma to the application; the ones
+restated here are the per-column L2 normalisation of power/Lanczos-style runs
+(reduced in FP64) and, for the graph-neural-network use the introduction
+motivates (a layer applies a non-linearity to A X), the rectifier max(0, y)
+and the per-row L2 normalisation.  They compose in one fixed order:
+sigma(Y) = column_normalise(row_normalise(relu(Y))), each part optional.
 
 Pinned by tests/test_oracle_spmm.py (closed-form stencil eigenvectors,
-row-normalised and GCN-normalised invariants, dense brute force).
+row-normalised and GCN-normalised invariants, dense brute force, and the fixed
+points and identities of the three sigma parts).
 """
 from __future__ import annotations
 
@@ -38,16 +43,37 @@ def column_normalise(Y: np.ndarray) -> np.ndarray:
     return Y / norms
 
 
-def iterate(A, X: np.ndarray, iters: int, rescale: bool = False) -> np.ndarray:
+def relu(Y: np.ndarray) -> np.ndarray:
+    """The rectifier applied entry by entry: y if y > 0, else 0."""
+    Y = np.asarray(Y, dtype=np.float64)
+    return np.where(Y > 0.0, Y, 0.0)
+
+
+def row_normalise(Y: np.ndarray) -> np.ndarray:
+    """Every row divided by its FP64 L2 norm; a row of zeros stays zero."""
+    Y = np.asarray(Y, dtype=np.float64)
+    norms = np.sqrt(np.sum(Y * Y, axis=1))
+    out = np.zeros_like(Y)
+    nz = norms > 0.0
+    out[nz] = Y[nz] / norms[nz][:, None]
+    return out
+
+
+def iterate(A, X: np.ndarray, iters: int, rescale: bool = False, rectify: bool = False,
+            rownorm: bool = False) -> np.ndarray:
     """X_T of X_{t+1} = sigma(A X_t), X_0 = X (Section 2).
 
-    sigma is the identity when ``rescale`` is false, else
-    :func:`column_normalise`.  Returns X_T in FP64.
+    sigma = column_normalise (if ``rescale``) after row_normalise (if ``rownorm``) after
+    relu (if ``rectify``); the identity when all are false.  Returns X_T in FP64.
     """
     S = A.to_scipy()
     Y = np.asarray(X, dtype=np.float64)
     for _ in range(iters):
         Y = np.asarray(S @ Y)
+        if rectify:
+            Y = relu(Y)
+        if rownorm:
+            Y = row_normalise(Y)
         if rescale:
             Y = column_normalise(Y)
     return Y

@@ -5,7 +5,12 @@
 * brute force (dense, entry by entry) on tiny inputs;
 * the iteration equals the dense matrix power, and with per-column rescaling it
   equals the normalised matrix power (scalars commute with A);
-* Eq. 1 (Section 3): sum_i P_i B_i P_i^T X equals A X for the oracle's own decomposition.
+* Eq. 1 (Section 3): sum_i P_i B_i P_i^T X equals A X for the oracle's own decomposition;
+* the sigma parts: the rectifier is the identity on non-negative data and zero on
+  non-positive data and splits y = relu(y) - relu(-y); row normalisation gives unit rows, is
+  blind to positive row scales and maps a rank-one u v^T to sign(u) v / |v|; a row-normalised
+  A keeps the all-ones block fixed under row normalisation, a GCN-normalised A keeps
+  d^{1/2} fixed under the rectifier and column normalisation.
 """
 import math
 
@@ -108,3 +113,49 @@ def test_iterate_rows_equals_full_iteration():
         full = S.iterate(A, X, T)[rows]
         assert np.allclose(S.iterate_rows(A, X, T, rows), full, rtol=1e-13, atol=1e-13)
         assert np.allclose(S.iterate_rows(A, lambda r: X[r], T, rows), full, rtol=1e-13, atol=1e-13)
+
+
+def test_relu_definition_and_fixed_points():
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((50, 6))
+    R = S.relu(Y)
+    assert np.all(R >= 0.0) and np.array_equal(S.relu(R), R)
+    assert np.array_equal(R - S.relu(-Y), Y)                    # y = max(0, y) - max(0, -y)
+    assert np.array_equal(R[Y > 0], Y[Y > 0]) and np.all(R[Y <= 0] == 0.0)
+    # a matrix with positive values: non-negative data stays as it was, non-positive data vanishes
+    A = w.grid_stencil((9, 7), seed=2)
+    Xp = np.abs(rng.standard_normal((A.n, 3)))
+    assert np.allclose(S.iterate(A, Xp, 4, rectify=True), S.iterate(A, Xp, 4), rtol=1e-14, atol=0)
+    assert np.count_nonzero(S.iterate(A, -Xp, 1, rectify=True)) == 0
+
+
+def test_row_normalise_definition_and_fixed_points():
+    rng = np.random.default_rng(4)
+    Y = rng.standard_normal((40, 5))
+    Y[7] = 0.0
+    N = S.row_normalise(Y)
+    nrm = np.linalg.norm(N, axis=1)
+    assert np.allclose(np.delete(nrm, 7), 1.0, atol=1e-15) and nrm[7] == 0.0
+    c = np.exp(rng.standard_normal(40))[:, None]
+    assert np.allclose(S.row_normalise(c * Y), N, rtol=1e-14, atol=1e-15)
+    u, v = rng.standard_normal(30), rng.standard_normal(4)
+    assert np.allclose(S.row_normalise(np.outer(u, v)), np.sign(u)[:, None] * v / np.linalg.norm(v), atol=1e-15)
+    # row-normalised A maps the all-ones block to itself, so 1 / sqrt(k) is a fixed point
+    A = w.grid3d(6, seed=3)
+    X1 = np.ones((A.n, 4))
+    assert np.allclose(S.iterate(A, X1, 5, rownorm=True), 0.5, atol=1e-14)
+
+
+def test_sigma_composition_on_gcn_fixed_point():
+    # GCN-normalised A fixes d^{1/2}; it is positive, so the rectifier keeps it and the
+    # column normalisation returns d^{1/2} / |d^{1/2}| after every step
+    A = w.rmat_gcn(9, 8, seed=8)
+    d = np.sqrt(np.diff(A.rowptr).astype(np.float64))
+    X = np.stack([d, 2 * d], axis=1)
+    Y = S.iterate(A, X, 6, rescale=True, rectify=True)
+    assert np.allclose(Y, (d / np.linalg.norm(d))[:, None], rtol=1e-12, atol=1e-14)
+    # the order is column(row(relu(.))): on the same data row normalisation makes each row
+    # (d_r, 2 d_r) / |.| = (1, 2) / sqrt(5), then the columns are normalised
+    Z = S.iterate(A, X, 1, rescale=True, rectify=True, rownorm=True)
+    ref = np.tile(np.array([1.0, 2.0]) / math.sqrt(5.0), (A.n, 1))
+    assert np.allclose(Z, ref / np.linalg.norm(ref, axis=0), rtol=1e-12)
