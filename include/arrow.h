@@ -39,10 +39,11 @@ typedef enum { ARROW_F32 = 0, ARROW_BF16 = 1, ARROW_F16 = 2 } arrow_dtype;
 
 /* ---- arrow predicates (shape of each B_i) ---------------------------------------- */
 /* Block-diagonal arrow (Section 3.1, Fig. 2, Alg. 1): entry at positions (r, c) belongs
- * to B_i iff r < b or c < b or floor(r/b) == floor(c/b).  The device path requires it. */
+ * to B_i iff r < b or c < b or floor(r/b) == floor(c/b).  The default. */
 #define ARROW_PRED_BLOCK 0
-/* Banded arrow (Section 1 definition, 0-based): r < b or c < b or |r - c| <= b.
- * Host-only (structure export); arrow_upload/arrow_spmm reject it with ARROW_EINVAL. */
+/* Banded arrow (Section 1 definition, 0-based): r < b or c < b or |r - c| <= b.  A band row
+ * reaches into three consecutive b x b tiles (block-tridiagonal).  The device path runs it
+ * through the same fused row program as the block form. */
 #define ARROW_PRED_BAND  1
 
 /* ---- input matrix ------------------------------------------------------------------ */
@@ -124,7 +125,8 @@ int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t it
 int arrow_decompose(const arrow_csr* A, int64_t b, const arrow_opts* o, arrow_handle* out);
 
 /* Upload a handle built with ARROW_HOST_ONLY to the current (or opts.device) GPU; the
- * caller's current device is left as it was.  No-op if already uploaded.  Errors: ARROW_EINVAL (band predicate), ARROW_ENOMEM, ARROW_ECUDA. */
+ * caller's current device is left as it was.  No-op if already uploaded.
+ * Errors: ARROW_ENOMEM, ARROW_ECUDA. */
 int arrow_upload(arrow_handle h);
 
 /* arrow_handle_copy -- a second handle with the same decomposition (no re-decomposition),
@@ -349,7 +351,7 @@ typedef struct {
     const int32_t* tile_row;    /* [n_tiles+1] first row of each tile */
     const int32_t* tile_ent;    /* [n_tiles+1] first short entry of each tile */
 } arrow_program;
-/* Errors: ARROW_EINVAL (NULL argument), ARROW_ESTATE (band-predicate handle: no program). */
+/* Errors: ARROW_EINVAL (NULL argument). */
 int arrow_get_program(arrow_handle h, arrow_program* out);
 
 /* Number of distinct non-zero b x b tiles of A in its own row and column order: the equally

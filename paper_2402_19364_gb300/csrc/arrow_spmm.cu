@@ -926,10 +926,6 @@ int arrow_decompose(const arrow_csr* A, int64_t b, const arrow_opts* o, arrow_ha
 int arrow_upload(arrow_handle h) {
     if (!h) { set_error("arrow_upload: NULL handle"); return ARROW_EINVAL; }
     if (h->uploaded) return ARROW_OK;
-    if (h->opts.predicate != ARROW_PRED_BLOCK) {
-        set_error("arrow_upload: the device path needs the block-diagonal predicate");
-        return ARROW_EINVAL;
-    }
     int rc;
     try {
         rc = upload_impl(h);
@@ -1109,7 +1105,6 @@ int arrow_set_tuning(arrow_handle h, const arrow_tuning* t) {
         set_error("arrow_set_tuning: tile too large for shared memory");
         return ARROW_EINVAL;
     }
-    if (h->opts.predicate != ARROW_PRED_BLOCK) { set_error("arrow_set_tuning: band-predicate handles have no device path"); return ARROW_EINVAL; }
     const bool retile = t->tile_rows != h->tune.tile_rows || t->tile_nnz != h->tune.tile_nnz;
     if (retile) {
         build_tiles(h, t->tile_rows, t->tile_nnz);

@@ -755,8 +755,12 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
     // column (the CSR order of B_i).  Each entry reads X row pi_0(column vertex).
     // Rows with more than long_row entries (the head rows of hubs) are split: their
     // entries move to a separate stream cut into fixed-size segments, and their range
-    // in the short-row stream is empty.
-    if (!band) {
+    // in the short-row stream is empty.  The program does not depend on the predicate: a
+    // row of B_i holds, beside its head columns, the columns of one diagonal tile (block
+    // predicate) or of the band |p - q| <= b, which spans three consecutive tiles (the
+    // block-tridiagonal form of the band predicate); either way the row's entries are read
+    // through the same index stream.
+    {
         std::vector<int32_t> iperm0(n);
         const int32_t* perm0 = nl ? h->levels[0].perm.data() : nullptr;
         if (nl) for (int64_t v = 0; v < n; ++v) iperm0[perm0[v]] = int32_t(v);
@@ -1056,7 +1060,7 @@ int arrow_get_level_shape(arrow_handle h, int32_t i, arrow_level_shape* out) {
 int arrow_get_program(arrow_handle h, arrow_program* out) {
     if (!h || !out) { arrow::set_error("arrow_get_program: NULL argument"); return ARROW_EINVAL; }
     if (h->f_rowptr.empty() && h->n > 0) {
-        arrow::set_error("arrow_get_program: band-predicate handles have no device program");
+        arrow::set_error("arrow_get_program: the handle has no device program");
         return ARROW_ESTATE;
     }
     out->n = h->n;

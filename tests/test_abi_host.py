@@ -142,10 +142,6 @@ def test_state_errors_without_gpu(arrow):
     assert rc == _native.ARROW_ESTATE                                        # not uploaded
     sz = ctypes.c_size_t()
     assert L.arrow_workspace_size(M._h, 16, 0, 0, ctypes.byref(sz)) == _native.ARROW_ESTATE
-    Mb = arrow.ArrowMatrix(w.grid2d_64(), 64, host_only=True, predicate="band")
-    with pytest.raises(arrow.ArrowError) as e:
-        Mb.upload()                                                          # band is host-only
-    assert e.value.code == _native.ARROW_EINVAL
     L.arrow_free(None)                                                       # NULL-safe
     assert L.arrow_level_info(M._h, 99, None, None) == _native.ARROW_EINVAL
 

@@ -54,9 +54,7 @@ def test_library_matches_oracle(n, density, seed, sym, diag, b, dseed, band, lon
         sh = M.level_shape(i)
         assert (sh["n_active"], sh["nnz"]) == (lv.n_active, lv.nnz)
         assert (sh["head_nnz"], sh["band_nnz"], sh["tiles"]) == D.level_shape(lv)
-    if band:
-        return
-    # the fused program evaluated as the kernels do equals the FP64 product
+    # the fused program evaluated as the kernels do equals the FP64 product (either predicate)
     pg = M.program()
     perm0 = M.level_perm(0).astype(np.int64) if M.num_levels else np.arange(n)
     iperm0 = np.empty(n, np.int64)

@@ -108,6 +108,36 @@ def test_rgg_fp16(arrow, k):
     assert err_2(Y, S.iterate(A, X, 10)) <= 2e-2
 
 
+@pytest.mark.parametrize("case", ["grid2d", "grid3d_rescale", "rmat_split_bf16", "rgg_f16"])
+def test_band_predicate_device_path(arrow, case):
+    """The band predicate of Section 1 (|p - q| <= b) on the device, against the oracle, and
+    against the block predicate's result on the same inputs (both are A X)."""
+    if case == "grid2d":
+        A, b, X, it, dt, kw, rs = w.grid2d_64(seed=1), 64, w.features(4096, 16, seed=2), 10, "f32", {}, False
+    elif case == "grid3d_rescale":
+        A = w.grid3d(24, seed=3)
+        b, X, it, dt, kw, rs = 96, w.features(A.n, 16, seed=4), 20, "f32", {}, True
+    elif case == "rmat_split_bf16":
+        A = w.rmat_gcn(12, 16, seed=5)
+        b, X, it, dt, kw, rs = 64, w.features(A.n, 64, seed=6), 4, "bf16", {"long_row": 16, "segment": 64}, False
+    else:
+        A = w.rgg(6000, seed=7)
+        b, X, it, dt, kw, rs = 78, w.features(A.n, 32, seed=8), 10, "f16", {}, False
+    Mb, _, Yb = run(arrow, A, b, X, it, dt=dt, rescale=rs, predicate="band", **kw)
+    Mk, _, Yk = run(arrow, A, b, X, it, dt=dt, rescale=rs, **kw)
+    R = S.iterate(A, X, it, rescale=rs)
+    if dt == "f32":
+        assert err_inf(Yb, R) <= 1e-5 * it
+        assert err_inf(Yb, Yk) <= 2e-5 * it
+    else:
+        assert err_2(Yb, R) <= 2e-2
+    # every entry lands in one level of the band decomposition
+    assert sum(Mb.level_info(i)[1] for i in range(Mb.num_levels)) == A.nnz
+    Mb2 = arrow.ArrowMatrix(A, b, value_dtype=dt, predicate="band", **kw)
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to("cuda", TORCH_DT[dt])
+    assert torch.equal(Mb.spmm(Xd, it, rescale=rs), Mb2.spmm(Xd, it, rescale=rs))   # fixed order
+
+
 def test_iters_zero_alias_and_determinism(arrow):
     A = w.grid_stencil((37, 29), seed=9)            # ragged: n = 1073 is not a multiple of b
     X = w.features(A.n, 32, seed=10)

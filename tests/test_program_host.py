@@ -43,9 +43,9 @@ CASES = {
 }
 
 
-def _entry_levels(A, b, seed=0):
+def _entry_levels(A, b, seed=0, pred="block"):
     """Level of every entry of A and its level-position column, from the oracle's decomposition."""
-    lv = D.la_decompose(A, b, seed=seed) if A.nnz else []
+    lv = D.la_decompose(A, b, seed=seed, predicate=D.pred_band if pred == "band" else D.pred_block) if A.nnz else []
     key = {}
     for i, L in enumerate(lv):
         rows = np.repeat(np.arange(L.n), np.diff(L.rowptr))
@@ -55,11 +55,12 @@ def _entry_levels(A, b, seed=0):
     return [key[(int(r), int(c))] for r, c in zip(arow, A.colidx)]
 
 
+@pytest.mark.parametrize("pred", ["block", "band"])
 @pytest.mark.parametrize("case", list(CASES))
-def test_program_layout_and_value(arrow, case):
+def test_program_layout_and_value(arrow, case, pred):
     make, b, kw = CASES[case]
     A = make()
-    M = arrow.ArrowMatrix(A, b, host_only=True, **kw)
+    M = arrow.ArrowMatrix(A, b, host_only=True, predicate=pred, **kw)
     pg = M.program()
     n, nnz = A.n, A.nnz
     perm0 = M.level_perm(0).astype(np.int64) if M.num_levels else np.arange(n)
@@ -110,7 +111,7 @@ def test_program_layout_and_value(arrow, case):
 
     # inside a short row: levels in order, inside a level increasing level position
     if nnz:
-        lvpos = _entry_levels(A, b)
+        lvpos = _entry_levels(A, b, pred=pred)
         keys = [lvpos[int(e)] for e in src]
         for p in range(n):
             k = keys[rp[p]:rp[p + 1]]
@@ -127,9 +128,3 @@ def test_program_layout_and_value(arrow, case):
     Y = Yh[perm0]
     R = S.spmm(A, X)
     assert np.allclose(Y, R, rtol=1e-12, atol=1e-12)
-
-
-def test_program_rejected_for_band_handles(arrow):
-    M = arrow.ArrowMatrix(w.grid2d_64(), 64, host_only=True, predicate="band")
-    with pytest.raises(arrow.ArrowError):
-        M.program()
