@@ -154,14 +154,22 @@ void arrow_free(arrow_handle h);
 /* ---- the hot path ------------------------------------------------------------------ */
 #define ARROW_RESCALE 0x1   /* spmm flags: sigma = per-column L2 normalisation (FP64 norms) */
 #define ARROW_PROFILE 0x2   /* spmm flags: record CUDA events around every kernel launch  */
+#define ARROW_RELU    0x8   /* spmm flags: sigma includes the rectifier max(0, y)          */
+#define ARROW_ROWNORM 0x10  /* spmm flags: sigma includes the per-row L2 normalisation     */
 
 /* arrow_spmm -- iters steps of X_{t+1} = sigma(A X_t), X_0 = X, result X_iters in Y.
  * A is applied as sum_i P_i B_i P_i^T X (Eq. 1, Alg. 1 / Alg. 2 computed on one GPU):
  * X is permuted into the first level's order once, every step runs the split head-row
  * reduction and the fused arrow-row kernel (all levels, fixed level order, no atomics),
  * and the result is permuted back once (Section 5.1: rows stay in pi_0 order between
- * iterations).  sigma is the identity, or with ARROW_RESCALE the division of every
- * column by its L2 norm, reduced in FP64.
+ * iterations).  sigma (Section 2 leaves it to the application) is composed from three
+ * optional parts in a fixed order, sigma(Y) = colnorm(rownorm(relu(Y))):
+ *   ARROW_RELU    -- max(0, y) on every element (the non-linearity of a graph-network
+ *                    layer, the use the introduction motivates), fused into the row store;
+ *   ARROW_ROWNORM -- every row divided by its L2 norm (zero rows stay zero), fused into the
+ *                    row store; needs k / (16 / sizeof(x_dtype)) <= 32;
+ *   ARROW_RESCALE -- every column divided by its L2 norm, reduced in FP64 (power/Lanczos).
+ * No flag: sigma is the identity.
  *   h       : uploaded handle.
  *   X, Y    : DEVICE pointers, row-major n x k, element type x_dtype, caller-owned.
  *             X and Y may be the same buffer.  Both must be 16-byte aligned.
@@ -169,7 +177,7 @@ void arrow_free(arrow_handle h);
  *             k / (16 / sizeof(x_dtype)) a power of two <= 32, or a multiple of 32.
  *   iters   : >= 0; iters = 0 copies X to Y.
  *   x_dtype : arrow_dtype of X and Y (FP32 accumulation in every case).
- *   flags   : 0, ARROW_RESCALE and/or ARROW_PROFILE.
+ *   flags   : 0 or any of ARROW_RESCALE, ARROW_RELU, ARROW_ROWNORM, ARROW_PROFILE.
  *   stream  : cudaStream_t; the call only enqueues work (no host synchronisation), except
  *             that the first call for a given (k, x_dtype) allocates the handle's workspace.
  * The handle's device must be the current device (ARROW_EINVAL otherwise, nothing launched).

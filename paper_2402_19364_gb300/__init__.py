@@ -14,7 +14,7 @@ import numpy as np
 from . import _native
 from ._native import (ARROW_BF16, ARROW_F16, ARROW_F32, ARROW_GRAPH, ARROW_HOST_ONLY, ARROW_K_NORM, ARROW_K_PERMUTE,
                       ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_PRED_BAND, ARROW_PRED_BLOCK, ARROW_PROFILE,
-                      ARROW_RESCALE, ArrowError)
+                      ARROW_RELU, ARROW_RESCALE, ARROW_ROWNORM, ArrowError)
 
 __all__ = ["ArrowMatrix", "ArrowBatch", "count_tiles", "ArrowServer", "ArrowError", "dtype_code", "ARROW_F32", "ARROW_BF16", "ARROW_F16"]
 
@@ -224,15 +224,18 @@ class ArrowMatrix:
             raise ValueError("X must be a contiguous CUDA tensor of shape (n, k)")
         return dtype_code(X.dtype)
 
-    def spmm(self, X, iters: int = 1, *, rescale: bool = False, out=None, stream=None, profile: bool = False):
-        """Y = X_iters of X_{t+1} = sigma(A X_t) through ``arrow_spmm`` (returns Y)."""
+    def spmm(self, X, iters: int = 1, *, rescale: bool = False, relu: bool = False, rownorm: bool = False,
+             out=None, stream=None, profile: bool = False):
+        """Y = X_iters of X_{t+1} = sigma(A X_t) through ``arrow_spmm`` (returns Y); sigma =
+        colnorm(rownorm(relu(.))) with each part switched by its argument."""
         import torch
         xd = self._check_x(X)
         if out is None:
             out = torch.empty_like(X)
         elif out.shape != X.shape or out.dtype != X.dtype or not out.is_contiguous():
             raise ValueError("out must match X")
-        flags = (ARROW_RESCALE if rescale else 0) | (ARROW_PROFILE if profile else 0)
+        flags = ((ARROW_RESCALE if rescale else 0) | (ARROW_PROFILE if profile else 0) | (ARROW_RELU if relu else 0)
+                 | (ARROW_ROWNORM if rownorm else 0))
         _native.check(_native.lib().arrow_spmm(self._h, ctypes.c_void_p(X.data_ptr()), X.shape[1], int(iters),
                                                ctypes.c_void_p(out.data_ptr()), xd, flags, _stream_ptr(stream)))
         return out

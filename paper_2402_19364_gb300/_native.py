@@ -21,6 +21,8 @@ ARROW_HOST_ONLY = 0x1
 ARROW_RESCALE = 0x1
 ARROW_PROFILE = 0x2
 ARROW_GRAPH = 0x4
+ARROW_RELU = 0x8
+ARROW_ROWNORM = 0x10
 ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_K_NORM, ARROW_K_PERMUTE = 0, 1, 2, 3
 
 

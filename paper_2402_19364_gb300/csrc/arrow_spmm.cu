@@ -72,7 +72,35 @@ struct RowArgs {
     double* norm_partials;     // [gridDim.x][k] (rows kernel slots), or null
     int32_t* status;
     int32_t rp_bytes, col_bytes, buf_bytes;   // shared-memory layout of a staged tile
+    int32_t sigma;             // kSigmaRelu | kSigmaRowNorm applied to each output row, or 0
 };
+
+// sigma applied to an output row held by a team of T lanes (V columns each) before it is
+// stored (Section 2 leaves sigma to the application; see arrow.h): the rectifier on every
+// element, then the division of the row by its L2 norm (the team's squares summed by an xor
+// butterfly inside the team, so every lane gets the same bits).  The column rescale, if on,
+// is applied afterwards through the next step's scale, which realises
+// column_normalise(row_normalise(relu(.))).
+constexpr int kSigmaRelu = 1;
+constexpr int kSigmaRowNorm = 2;
+template <int T, int V>
+__device__ __forceinline__ void apply_sigma(float* acc, int sigma, int lane) {
+    if (sigma & kSigmaRelu) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = fmaxf(acc[v], 0.f);
+    }
+    if (sigma & kSigmaRowNorm) {
+        float ss = 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) ss = fmaf(acc[v], acc[v], ss);
+        const unsigned mask = T == 32 ? 0xffffffffu : (((1u << T) - 1u) << (lane & ~(T - 1)));
+#pragma unroll
+        for (int off = 1; off < T; off <<= 1) ss += __shfl_xor_sync(mask, ss, off);
+        const float inv = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] *= inv;
+    }
+}
 
 // Thread 0: stage tile t (row pointers, columns, values) into buf with three bulk copies.
 template <typename TV>
@@ -171,6 +199,7 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+            if (a.sigma) apply_sigma<T, V>(acc, a.sigma, lane);
             const uint4 out = P::from_float(acc);
             st_y(Y + int64_t(r0 + j) * a.ldx, out);
             if (RESCALE) {
@@ -279,6 +308,7 @@ struct CombArgs {
     int32_t koff, kc;
     const double* scale;
     double* norm_partials;     // [gridDim.x][k] (combine slots), or null
+    int32_t sigma;
 };
 
 // Second stage of the head-row reduction: a team per split row adds its segment partials
@@ -314,6 +344,7 @@ __global__ void __launch_bounds__(256) arrow_combine_kernel(CombArgs a) {
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+        if (a.sigma) apply_sigma<T, V>(acc, a.sigma, lane);
         const uint4 out = P::from_float(acc);
         *reinterpret_cast<uint4*>(Y + int64_t(__ldg(a.long_rows + li)) * a.ldx) = out;
         if (RESCALE) {
@@ -653,6 +684,10 @@ static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags,
         p.T = 32; p.chunks = int(t / 32);
     }
     p.kc = p.T * p.V;
+    if ((flags & ARROW_ROWNORM) && p.chunks > 1) {
+        set_error("arrow_spmm: ARROW_ROWNORM needs a whole row in one team: k / (16 / sizeof(dtype)) <= 32");
+        return ARROW_EINVAL;
+    }
     const int sm = h->dev.sm_count > 0 ? h->dev.sm_count : 1;
     // persistent rows kernel: ctas_per_sm CTAs per SM, capped by the variant's register bound
     // (one FP64 norm slot each)
@@ -671,9 +706,13 @@ static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags,
     return ARROW_OK;
 }
 
+static int sigma_of(int flags) {
+    return ((flags & ARROW_RELU) ? kSigmaRelu : 0) | ((flags & ARROW_ROWNORM) ? kSigmaRowNorm : 0);
+}
+
 template <typename TX, typename TV, int T>
 static void launch_step(const arrow_handle_s* h, const Plan& p, const TX* cur, TX* nxt, int64_t k, float* part,
-                        const double* scale_in, double* np, cudaStream_t s, Prof& pf) {
+                        const double* scale_in, double* np, int sigma, cudaStream_t s, Prof& pf) {
     const DeviceData& d = h->dev;
     const int32_t n_tiles = h->tile_row.empty() ? 0 : int32_t(h->tile_row.size()) - 1;
     for (int ch = 0; ch < p.chunks; ++ch) {
@@ -688,7 +727,7 @@ static void launch_step(const arrow_handle_s* h, const Plan& p, const TX* cur, T
         }
         const TileLayout L = tile_layout(h->tune.tile_rows, h->tune.tile_nnz);
         RowArgs ra{d.rowptr, d.col, d.val, d.tile_row, d.tile_ent, n_tiles, cur, nxt, k, koff, p.kc, scale_in, np,
-                   d.status, L.rp, L.col, L.buf};
+                   d.status, L.rp, L.col, L.buf, sigma};
         const int smem = rows_smem_bytes(L, np ? (256 / T) * p.kc : 0);
         cudaEvent_t e0 = pf.begin();
         if (np) {
@@ -701,7 +740,7 @@ static void launch_step(const arrow_handle_s* h, const Plan& p, const TX* cur, T
         pf.end(ARROW_K_ROWS, e0);
         if (p.comb_grid) {
             CombArgs ca{d.long_rows, d.long_segptr, int32_t(h->long_rows.size()), part, nxt, k, koff, p.kc, scale_in,
-                        np ? np + size_t(p.rows_grid) * size_t(k) : nullptr};
+                        np ? np + size_t(p.rows_grid) * size_t(k) : nullptr, sigma};
             cudaEvent_t e1 = pf.begin();
             if (np)
                 arrow_combine_kernel<TX, T, true><<<p.comb_grid, 256, 0, s>>>(ca);
@@ -721,13 +760,14 @@ static void run_steps(const arrow_handle_s* h, const Plan& p, TX* xa, TX* xb, in
     for (int t = 1; t <= iters; ++t) {
         const double* sin = (rescale && t > 1) ? sc + ((t - 1) & 1) * k : nullptr;
         double* npo = rescale ? np : nullptr;
+        const int sg = sigma_of(flags);
         switch (p.T) {
-            case 1: launch_step<TX, TV, 1>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
-            case 2: launch_step<TX, TV, 2>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
-            case 4: launch_step<TX, TV, 4>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
-            case 8: launch_step<TX, TV, 8>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
-            case 16: launch_step<TX, TV, 16>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
-            default: launch_step<TX, TV, 32>(h, p, cur, nxt, k, part, sin, npo, s, pf); break;
+            case 1: launch_step<TX, TV, 1>(h, p, cur, nxt, k, part, sin, npo, sg, s, pf); break;
+            case 2: launch_step<TX, TV, 2>(h, p, cur, nxt, k, part, sin, npo, sg, s, pf); break;
+            case 4: launch_step<TX, TV, 4>(h, p, cur, nxt, k, part, sin, npo, sg, s, pf); break;
+            case 8: launch_step<TX, TV, 8>(h, p, cur, nxt, k, part, sin, npo, sg, s, pf); break;
+            case 16: launch_step<TX, TV, 16>(h, p, cur, nxt, k, part, sin, npo, sg, s, pf); break;
+            default: launch_step<TX, TV, 32>(h, p, cur, nxt, k, part, sin, npo, sg, s, pf); break;
         }
         if (rescale) {
             cudaEvent_t e0 = pf.begin();
@@ -775,7 +815,10 @@ static int check_spmm_args(const arrow_handle_s* h, const void* X, int64_t k, in
     if (!h->uploaded) { set_error("arrow_spmm: handle is not uploaded (decomposed with ARROW_HOST_ONLY?)"); return ARROW_ESTATE; }
     if (k < 0 || iters < 0) { set_error("arrow_spmm: k and iters must be >= 0"); return ARROW_EINVAL; }
     if (!dtype_ok(x_dtype)) { set_error("arrow_spmm: unknown x_dtype"); return ARROW_EINVAL; }
-    if (flags & ~(ARROW_RESCALE | ARROW_PROFILE)) { set_error("arrow_spmm: unknown flags"); return ARROW_EINVAL; }
+    if (flags & ~(ARROW_RESCALE | ARROW_PROFILE | ARROW_RELU | ARROW_ROWNORM)) {
+        set_error("arrow_spmm: unknown flags");
+        return ARROW_EINVAL;
+    }
     if (x_dtype == ARROW_F32 && h->opts.value_dtype != ARROW_F32) {
         set_error("arrow_spmm: F32 features need F32 values");
         return ARROW_EINVAL;

@@ -138,6 +138,44 @@ def test_band_predicate_device_path(arrow, case):
     assert torch.equal(Mb.spmm(Xd, it, rescale=rs), Mb2.spmm(Xd, it, rescale=rs))   # fixed order
 
 
+@pytest.mark.parametrize("dt,k,relu,rownorm,rescale", [
+    ("f32", 16, True, False, False), ("f32", 16, False, True, False), ("f32", 32, True, True, True),
+    ("f32", 128, True, True, False), ("bf16", 64, True, False, False), ("bf16", 256, False, True, True),
+    ("f16", 8, True, True, False)])
+def test_sigma_epilogues(arrow, dt, k, relu, rownorm, rescale):
+    """sigma = colnorm(rownorm(relu(.))) fused into the row stores, on a grid and on a power-law
+    matrix whose hub rows are split (their rows are written by the combine kernel)."""
+    iters = 5
+    for A, b, kw in ((w.grid_stencil((45, 38), seed=9), 45, {}),
+                     (w.rmat_gcn(11, 16, seed=5), 64, {"long_row": 16, "segment": 32})):
+        X = w.features(A.n, k, seed=k)
+        M = arrow.ArrowMatrix(A, b, value_dtype=dt, **kw)
+        Xd = torch.from_numpy(X).to("cuda", TORCH_DT[dt])
+        Y = M.spmm(Xd, iters, relu=relu, rownorm=rownorm, rescale=rescale)
+        torch.cuda.synchronize()
+        Y = Y.float().cpu().numpy().astype(np.float64)
+        R = S.iterate(A, X, iters, rescale=rescale, rectify=relu, rownorm=rownorm)
+        if dt == "f32":
+            assert err_inf(Y, R) <= 1e-5 * iters
+        else:
+            assert err_2(Y, R) <= 2e-2
+        if relu and not rownorm:
+            assert float(Y.min()) >= 0.0
+        if rownorm and not rescale:
+            nrm = np.linalg.norm(Y, axis=1)
+            assert np.allclose(nrm[nrm > 0], 1.0, atol=1e-5 if dt == "f32" else 1e-2)
+
+
+def test_sigma_rownorm_needs_one_team_per_row(arrow):
+    from paper_2402_19364_gb300 import _native
+    M = arrow.ArrowMatrix(w.grid2d_64(), 64)
+    with pytest.raises(arrow.ArrowError) as e:
+        M.spmm(torch.zeros(4096, 256, device="cuda"), 1, rownorm=True)   # 64 vectors of 16 B: two chunks
+    assert e.value.code == _native.ARROW_EINVAL
+    Y = M.spmm(torch.zeros(4096, 256, device="cuda"), 1, relu=True)    # the rectifier works per element
+    assert torch.count_nonzero(Y).item() == 0
+
+
 def test_iters_zero_alias_and_determinism(arrow):
     A = w.grid_stencil((37, 29), seed=9)            # ragged: n = 1073 is not a multiple of b
     X = w.features(A.n, 32, seed=10)
