@@ -908,7 +908,7 @@ namespace arrow {
 namespace {
 
 constexpr char kMagic[8] = {'A', 'R', 'W', 'D', 'E', 'C', '1', '\0'};
-constexpr int64_t kVersion = 2;
+constexpr int64_t kVersion = 3;
 
 struct Writer {
     FILE* f;

@@ -176,6 +176,32 @@ def test_sigma_rownorm_needs_one_team_per_row(arrow):
     assert torch.count_nonzero(Y).item() == 0
 
 
+@pytest.mark.parametrize("dt,k,rescale", [("f32", 16, True), ("bf16", 128, False), ("f16", 32, False)])
+def test_fold_and_l2_hints_keep_the_bits(arrow, dt, k, rescale):
+    """The permute-in folded into the first iteration and the L2 residency hints change where
+    data comes from, not the arithmetic: results are bit-identical to the plain path, and
+    match the oracle.  A 1 MB hot budget makes the hints engage on a small power-law matrix."""
+    A = w.rmat_gcn(13, 16, seed=5)
+    X = w.features(A.n, k, seed=3)
+    M = arrow.ArrowMatrix(A, 128, value_dtype=dt, long_row=32, segment=128)
+    Xd = torch.from_numpy(X).to("cuda", TORCH_DT[dt])
+    t = M.tuning
+    M.set_tuning(t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"], 0, 0)
+    ref = M.spmm(Xd, 6, rescale=rescale)
+    for hot_mb, fold in ((1, 0), (0, 1), (1, 1), (64, 1)):
+        M.set_tuning(t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"], hot_mb, fold)
+        Xa = Xd.clone()
+        Y = M.spmm(Xa, 6, rescale=rescale)
+        torch.cuda.synchronize()
+        assert torch.equal(Y, ref), (hot_mb, fold)
+        assert torch.equal(Xa, Xd)                               # the caller's X is only read
+        M.spmm(Xa, 6, rescale=rescale, out=Xa)                  # X and Y may alias with the fold
+        assert torch.equal(Xa, ref)
+    R = S.iterate(A, X, 6, rescale=rescale)
+    Yn = ref.float().cpu().numpy().astype(np.float64)
+    assert (err_inf(Yn, R) <= 6e-5) if dt == "f32" else (err_2(Yn, R) <= 2e-2)
+
+
 def test_iters_zero_alias_and_determinism(arrow):
     A = w.grid_stencil((37, 29), seed=9)            # ragged: n = 1073 is not a multiple of b
     X = w.features(A.n, 32, seed=10)
