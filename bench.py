@@ -59,7 +59,7 @@ def parse():
     p.add_argument("--no-fp32", action="store_true", help="skip the FP32 arm of a 16-bit workload")
     p.add_argument("--no-sub", action="store_true", help="default workload only: skip the other configurations' records")
     p.add_argument("--sub", default="grid2d,rmat,batch,serve", help="which other configurations to attach")
-    p.add_argument("--tuning", default="", help="tile_rows,tile_nnz,ctas_per_sm,carveout[,l2_hot_mb]: fixed tuning "
+    p.add_argument("--tuning", default="", help="tile_rows,tile_nnz,ctas_per_sm,carveout[,fold_permute_in]: fixed tuning "
                    "instead of autotuning (keeps a profiler's launch list short)")
     return p.parse_args()
 
@@ -70,7 +70,7 @@ def fixed_tuning(a):
         return None
     t = tuple(int(v) for v in a.tuning.split(","))
     if len(t) not in (4, 5):
-        raise SystemExit("--tuning wants tile_rows,tile_nnz,ctas_per_sm,carveout[,l2_hot_mb]")
+        raise SystemExit("--tuning wants tile_rows,tile_nnz,ctas_per_sm,carveout[,fold_permute_in]")
     return t
 
 

@@ -84,20 +84,16 @@ int arrow_opts_default(arrow_opts* o);
 /* How the fused row program is cut and launched (not in the paper; a property of this GPU
  * path): rows per tile, entries per tile (>= 1024, so every unsplit row fits), resident CTAs
  * per SM of the persistent rows kernel (1..4; with ARROW_RESCALE at most 3 are used, the
- * register bound of that variant), the shared-memory carveout in percent, and l2_hot_mb: the
- * megabytes of L2 that the X rows read most often (by the number of entries in their column)
- * may hold, kept there with an evict_last hint while the others are read evict_first; 0
- * turns these hints off, and they stay off when no such set of rows fits (uniform degrees).
- * fold_permute_in = 1 makes the first iteration gather straight from the caller's X through a
- * second copy of the column indices in vertex ids (4 bytes per entry of device memory, set up
- * when the setting is applied), instead of permuting X into pi_0 order first.
- * Defaults: 256, 2048, 4, 70, 64, 0. */
+ * register bound of that variant), the shared-memory carveout in percent, and
+ * fold_permute_in = 1, which makes the first iteration gather straight from the caller's X
+ * through a second copy of the column indices in vertex ids (4 bytes per entry of device
+ * memory, set up when the setting is applied) instead of permuting X into pi_0 order first.
+ * Defaults: 256, 2048, 4, 70, 0. */
 typedef struct {
     int32_t tile_rows;
     int32_t tile_nnz;
     int32_t ctas_per_sm;
     int32_t carveout;
-    int32_t l2_hot_mb;
     int32_t fold_permute_in;
 } arrow_tuning;
 
@@ -110,15 +106,15 @@ int arrow_get_tuning(arrow_handle h, arrow_tuning* t);
 /* Re-tile the handle (host, O(n)) and, if uploaded, replace its device tile tables; waits for
  * the device first.  Errors: ARROW_EINVAL (out of range: 32 <= tile_rows <= 2048,
  * 1024 <= tile_nnz <= 16384, 1 <= ctas_per_sm <= 4, 0 <= carveout <= 100,
- * 0 <= l2_hot_mb <= 1024, fold_permute_in 0 or 1), ARROW_ENOMEM, ARROW_ECUDA. */
+ * fold_permute_in 0 or 1), ARROW_ENOMEM, ARROW_ECUDA. */
 int arrow_set_tuning(arrow_handle h, const arrow_tuning* t);
 
 /* arrow_autotune -- time a fixed set of tunings (tile shapes 128/1024, 256/2048, 384/3072,
  * 512/4096 rows/entries x 2..4 CTAs per SM that fit, carveout fitted to them; then the best of
  * those with fold_permute_in switched) with arrow_spmm on the caller's X, Y (as arrow_spmm) for
  * `iters` iterations each (one warm-up call, two timed), keep the fastest on the handle, and
- * return it with its milliseconds per call.  l2_hot_mb is kept as set.  Synchronises
- * `stream`.  Errors: as arrow_spmm and arrow_set_tuning. */
+ * return it with its milliseconds per call.  Synchronises `stream`.
+ * Errors: as arrow_spmm and arrow_set_tuning. */
 int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t iters, int32_t x_dtype,
                    int32_t flags, void* stream, arrow_tuning* best, double* best_ms);
 

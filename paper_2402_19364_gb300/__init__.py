@@ -253,14 +253,10 @@ class ArrowMatrix:
         return {f: getattr(t, f) for f, _ in t._fields_}
 
     def set_tuning(self, tile_rows: int, tile_nnz: int, ctas_per_sm: int, carveout: int,
-                   l2_hot_mb: int | None = None, fold_permute_in: int | None = None) -> None:
-        cur = self.tuning
-        if l2_hot_mb is None:
-            l2_hot_mb = cur["l2_hot_mb"]
+                   fold_permute_in: int | None = None) -> None:
         if fold_permute_in is None:
-            fold_permute_in = cur["fold_permute_in"]
-        t = _native.ArrowTuning(int(tile_rows), int(tile_nnz), int(ctas_per_sm), int(carveout), int(l2_hot_mb),
-                                int(fold_permute_in))
+            fold_permute_in = self.tuning["fold_permute_in"]
+        t = _native.ArrowTuning(int(tile_rows), int(tile_nnz), int(ctas_per_sm), int(carveout), int(fold_permute_in))
         _native.check(_native.lib().arrow_set_tuning(self._h, ctypes.byref(t)))
 
     def autotune(self, X, iters: int, *, rescale: bool = False, out=None, stream=None):

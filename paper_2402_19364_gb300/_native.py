@@ -65,7 +65,7 @@ class ArrowProgram(ctypes.Structure):
 
 class ArrowTuning(ctypes.Structure):
     _fields_ = [("tile_rows", ctypes.c_int32), ("tile_nnz", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("carveout", ctypes.c_int32), ("l2_hot_mb", ctypes.c_int32), ("fold_permute_in", ctypes.c_int32)]
+                ("carveout", ctypes.c_int32), ("fold_permute_in", ctypes.c_int32)]
 
 
 class ArrowServerOpts(ctypes.Structure):

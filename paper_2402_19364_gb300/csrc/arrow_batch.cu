@@ -251,7 +251,6 @@ int arrow_batch_spmm(arrow_batch B, const void* const* X, void* const* Y, const 
             md.xb = p; p += xb;
             md.partials = reinterpret_cast<float*>(p); p += al256(std::max<size_t>(1, h->seg_begin.size()) * size_t(k[m]) * 4);
             md.n = h->n; md.k = k[m]; md.T = int32_t(k[m] / V);
-            md.col_mask = h->col_classes ? kClassMask : 0xffffffffu;
             B->h_desc[m] = md;
         }
         BCK(cudaMemcpy(B->d_desc, B->h_desc.data(), n_m * sizeof(MatDesc), cudaMemcpyHostToDevice));
@@ -306,7 +305,7 @@ int arrow_batch_autotune(arrow_batch B, const void* const* X, void* const* Y, co
             const TileLayout L = tile_layout(sh[0], sh[1]);
             const int per = batch_smem_bytes(L) + 1024;
             const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);
-            arrow_tuning cand{sh[0], sh[1], ctas, pct, B->hs[0]->tune.l2_hot_mb, B->hs[0]->tune.fold_permute_in};
+            arrow_tuning cand{sh[0], sh[1], ctas, pct, B->hs[0]->tune.fold_permute_in};
             if ((rc = apply(cand))) break;
             if ((rc = arrow_batch_spmm(B, X, Y, k, iters, x_dtype, ARROW_GRAPH, stream))) break;
             cudaEventRecord(e0, s);

@@ -39,9 +39,6 @@ constexpr int kMinTileNnz = 1024;    // split threshold never exceeds this, so e
 constexpr int kMaxTileRows = 2048;
 constexpr int kMaxTileNnz = 16384;
 constexpr int kDefaultSegment = 512;
-// Megabytes of L2 a launch may fill with the X rows it reads most often (see the gather
-// policies in device_common.cuh); 0 turns the residency hints off.
-constexpr int kDefaultL2HotMB = 64;
 
 // One level i of the decomposition A = sum_i P_{pi_i} B_i P_{pi_i}^T.
 struct Level {
@@ -104,12 +101,7 @@ struct arrow_handle_s {
     std::vector<int32_t> long_rows, long_segptr, seg_begin, seg_end;
     std::vector<int32_t> tile_row, tile_ent;
     int32_t long_row = arrow::kDefaultLongRow;
-    arrow_tuning tune{arrow::kTileRows, arrow::kTileNnz, 4, 70, arrow::kDefaultL2HotMB, 0};
-    // access classes of the X rows (set at upload): the device column indices carry them when
-    // n < 2^27; class_rows[c] = number of X rows of class c
-    bool col_classes = false;
-    int64_t class_rows[16] = {};
-    std::vector<uint8_t> pos_class;     // class of every pi_0 position's X row
+    arrow_tuning tune{arrow::kTileRows, arrow::kTileNnz, 4, 70, 0};
     double decompose_seconds = 0.0;
     bool uploaded = false;
     // bumped whenever the device arrays or the tile table change (upload, re-tiling):

@@ -339,7 +339,6 @@ static int server_step(arrow_server_s* S, void* stream, int32_t* active_out) {
         md.xa = p; md.xb = p + xb;
         md.partials = reinterpret_cast<float*>(p + 2 * xb);
         md.n = h->n; md.k = r.k; md.T = int32_t(r.k / V);
-        md.col_mask = h->col_classes ? kClassMask : 0xffffffffu;
         const bool iterate = r.left > 0;
         const bool finish = r.left <= 1;
         md.flip = iterate ? r.parity : 1;   // a request with no iteration leaves its result in xa

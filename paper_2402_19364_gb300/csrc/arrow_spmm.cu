@@ -73,8 +73,6 @@ struct RowArgs {
     int32_t* status;
     int32_t rp_bytes, col_bytes, buf_bytes;   // shared-memory layout of a staged tile
     int32_t sigma;             // kSigmaRelu | kSigmaRowNorm applied to each output row, or 0
-    uint32_t col_mask;         // strips the access-class bits of the column indices
-    int32_t hot_cls;           // X rows of class >= hot_cls are kept in L2 (kNoHints: off)
 };
 
 // sigma applied to an output row held by a team of T lanes (V columns each) before it is
@@ -137,7 +135,6 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
     const TX* __restrict__ X = static_cast<const TX*>(a.X) + a.koff + col0;
     TX* __restrict__ Y = static_cast<TX*>(a.Y) + a.koff + col0;
     const int G = gridDim.x;
-    const Gather gp = make_gather(a.col_mask, a.hot_cls);
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < kStages; ++b) {
@@ -157,9 +154,11 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
                 issue_tile<TV>(a, blockIdx.x + b * G, bufs + b * a.buf_bytes, &ps->full[b]);
                 ps->issued[b]++;
             }
+    // the previous step's column factors (only with the rescale: otherwise there are none, and
+    // the registers are left to the gathers)
     float scl[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) scl[v] = a.scale ? float(a.scale[a.koff + col0 + v]) : 1.0f;
+    for (int v = 0; v < V; ++v) scl[v] = (RESCALE && a.scale) ? float(a.scale[a.koff + col0 + v]) : 1.0f;
     float sq[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) sq[v] = 0.f;
@@ -188,7 +187,7 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
                 uint4 x[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (u < cnt) x[u] = gather_x(X, uint32_t(scol[base + u]), a.ldx, gp);
+                    if (u < cnt) x[u] = ld_x(X + int64_t(scol[base + u]) * a.ldx);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     if (u < cnt) {
@@ -200,8 +199,10 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
                     }
                 }
             }
+            if (RESCALE) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+                for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+            }
             if (a.sigma) apply_sigma<T, V>(acc, a.sigma, lane);
             const uint4 out = P::from_float(acc);
             st_y(Y + int64_t(r0 + j) * a.ldx, out);
@@ -269,8 +270,6 @@ struct SegArgs {
     int64_t ldx;
     int32_t koff, kc;
     float* partials;   // [n_seg][kc]
-    uint32_t col_mask;
-    int32_t hot_cls;
 };
 
 // One warp per segment of a split row (segment_partial), teams combined with a fixed xor
@@ -287,11 +286,10 @@ __global__ void __launch_bounds__(256, ARROW_SEG_MIN_BLOCKS) arrow_segments_kern
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     const TX* __restrict__ X = static_cast<const TX*>(a.X) + a.koff + col0;
     const TV* __restrict__ val = static_cast<const TV*>(a.val);
-    const Gather gp = make_gather(a.col_mask, a.hot_cls);
     for (int64_t g = warp0; g < a.n_seg; g += nwarps) {
         const int32_t s = __ldg(a.seg_begin + g), e = __ldg(a.seg_end + g);
         float acc[V];
-        segment_partial<TX, TV, T>(a.col, val, X, a.ldx, s, e, lane, acc, gp);
+        segment_partial<TX, TV, T>(a.col, val, X, a.ldx, s, e, lane, acc);
 #pragma unroll
         for (int off = T; off < 32; off <<= 1)
 #pragma unroll
@@ -331,7 +329,7 @@ __global__ void __launch_bounds__(256) arrow_combine_kernel(CombArgs a) {
     TX* __restrict__ Y = static_cast<TX*>(a.Y) + a.koff + col0;
     float scl[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) scl[v] = a.scale ? float(a.scale[a.koff + col0 + v]) : 1.0f;
+    for (int v = 0; v < V; ++v) scl[v] = (RESCALE && a.scale) ? float(a.scale[a.koff + col0 + v]) : 1.0f;
     double dsq[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) dsq[v] = 0.0;
@@ -348,8 +346,10 @@ __global__ void __launch_bounds__(256) arrow_combine_kernel(CombArgs a) {
                 acc[4 * q + 0] += f.x; acc[4 * q + 1] += f.y; acc[4 * q + 2] += f.z; acc[4 * q + 3] += f.w;
             }
         }
+        if (RESCALE) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+            for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+        }
         if (a.sigma) apply_sigma<T, V>(acc, a.sigma, lane);
         const uint4 out = P::from_float(acc);
         *reinterpret_cast<uint4*>(Y + int64_t(__ldg(a.long_rows + li)) * a.ldx) = out;
@@ -590,40 +590,12 @@ static int upload_values(const arrow_handle_s* h, const std::vector<int32_t>& sr
 
 static int upload_to_current(arrow_handle_s* h);
 
-// Access class of every pi_0 position's X row: min(15, bit length of the number of entries of
-// A in that vertex's column), i.e. of the gathers of that row per iteration.  Stored in the
-// device column indices (bits 27..30) when n < 2^27.
-static void encode_classes(arrow_handle_s* h) {
-    const int64_t n = h->n;
-    for (int c = 0; c < 16; ++c) h->class_rows[c] = 0;
-    h->col_classes = n > 0 && n < (int64_t(1) << kClassShift);
-    if (!h->col_classes) return;
-    std::vector<int32_t> cnt(n, 0);
-    for (int32_t c : h->colidx) cnt[c]++;
-    h->pos_class.assign(n, 0);
-    const int32_t* perm0 = h->levels.empty() ? nullptr : h->levels[0].perm.data();
-    for (int64_t v = 0; v < n; ++v) {
-        uint32_t x = uint32_t(cnt[v]);
-        int cls = 0;
-        while (x) { ++cls; x >>= 1; }
-        cls = std::min(cls, 15);
-        h->pos_class[perm0 ? perm0[v] : v] = uint8_t(cls);
-        h->class_rows[cls]++;
-    }
-}
-
-static void encoded_cols(const arrow_handle_s* h, const std::vector<int32_t>& col, std::vector<int32_t>& out) {
-    out.resize(col.size());
-    for (size_t j = 0; j < col.size(); ++j)
-        out[j] = int32_t(uint32_t(col[j]) | (uint32_t(h->pos_class[col[j]]) << kClassShift));
-}
-
 template <typename T>
 static int upload_vec(T** dst, const std::vector<T>& src, size_t& bytes);
 
-// The column indices as vertex ids (pi_0^{-1} of the stored positions, with the same class
-// bits), for a first iteration that gathers straight from the caller's X.  Uploaded when
-// fold_permute_in is set; kept until the handle is freed.
+// The column indices as vertex ids (pi_0^{-1} of the stored positions), for a first
+// iteration that gathers straight from the caller's X.  Uploaded when fold_permute_in is set;
+// kept until the handle is freed.
 static int upload_vertex_cols(arrow_handle_s* h) {
     DeviceData& d = h->dev;
     if (d.col_v || d.lcol_v || (h->f_col.empty() && h->l_col.empty())) return ARROW_OK;
@@ -635,10 +607,7 @@ static int upload_vertex_cols(arrow_handle_s* h) {
         for (int64_t v = 0; v < n; ++v) iperm0[v] = int32_t(v);
     auto convert = [&](const std::vector<int32_t>& col, std::vector<int32_t>& out) {
         out.resize(col.size());
-        for (size_t j = 0; j < col.size(); ++j) {
-            const uint32_t cls = h->col_classes ? uint32_t(h->pos_class[col[j]]) << kClassShift : 0u;
-            out[j] = int32_t(uint32_t(iperm0[col[j]]) | cls);
-        }
+        for (size_t j = 0; j < col.size(); ++j) out[j] = iperm0[col[j]];
     };
     std::vector<int32_t> tmp;
     int rc;
@@ -669,17 +638,8 @@ static int upload_to_current(arrow_handle_s* h) {
     ACK(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, d.device));
     int rc;
     if ((rc = upload_vec(&d.rowptr, h->f_rowptr, d.bytes))) return rc;
-    encode_classes(h);
-    if (h->col_classes) {
-        std::vector<int32_t> enc;
-        encoded_cols(h, h->f_col, enc);
-        if ((rc = upload_vec(&d.col, enc, d.bytes))) return rc;
-        encoded_cols(h, h->l_col, enc);
-        if ((rc = upload_vec(&d.lcol, enc, d.bytes))) return rc;
-    } else {
-        if ((rc = upload_vec(&d.col, h->f_col, d.bytes))) return rc;
-        if ((rc = upload_vec(&d.lcol, h->l_col, d.bytes))) return rc;
-    }
+    if ((rc = upload_vec(&d.col, h->f_col, d.bytes))) return rc;
+    if ((rc = upload_vec(&d.lcol, h->l_col, d.bytes))) return rc;
     if ((rc = upload_vec(&d.tile_row, h->tile_row, d.bytes))) return rc;
     if ((rc = upload_vec(&d.tile_ent, h->tile_ent, d.bytes))) return rc;
     if ((rc = upload_vec(&d.long_rows, h->long_rows, d.bytes))) return rc;
@@ -708,7 +668,6 @@ static int upload_to_current(arrow_handle_s* h) {
 // ---- launch plumbing -----------------------------------------------------------------
 struct Plan {
     int V, T, chunks, kc;
-    int hot_cls;     // gather residency threshold of this call (kNoHints: off)
     int rows_grid;   // CTAs of the rows kernel (= its FP64 norm partial slots)
     int comb_grid;   // CTAs of the combine kernel (= its partial slots after the rows kernel's)
     size_t x_bytes, part_bytes, np_bytes, sc_bytes, total;
@@ -748,23 +707,6 @@ int require_device(int device, const char* what) {
     return ARROW_OK;
 }
 
-// Residency threshold of a launch whose gathers read row_bytes of each X row: the lowest
-// class c such that the rows of classes >= c fit in tune.l2_hot_mb; kNoHints when the hints
-// are off, when no class fits, or when every row fits (nothing to protect).
-static int hot_class(const arrow_handle_s* h, size_t row_bytes) {
-    if (!h->col_classes || h->tune.l2_hot_mb <= 0) return kNoHints;
-    const double budget = double(h->tune.l2_hot_mb) * 1048576.0;
-    double bytes = 0.0;
-    int thr = kNoHints;
-    for (int c = 15; c >= 1; --c) {
-        bytes += double(h->class_rows[c]) * double(row_bytes);
-        if (bytes > budget) break;
-        thr = c;
-    }
-    if (thr <= 1) return kNoHints;   // every row read at all fits: plain loads
-    return thr;
-}
-
 static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags, Plan& p) {
     p.V = int(16 / dtype_size(x_dtype));
     if (k % p.V) { set_error("arrow_spmm: k * sizeof(dtype) must be a multiple of 16 bytes"); return ARROW_EINVAL; }
@@ -782,7 +724,6 @@ static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags,
         return ARROW_EINVAL;
     }
     const int sm = h->dev.sm_count > 0 ? h->dev.sm_count : 1;
-    p.hot_cls = hot_class(h, size_t(p.kc) * dtype_size(x_dtype));
     // persistent rows kernel: ctas_per_sm CTAs per SM, capped by the variant's register bound
     // (one FP64 norm slot each)
     const int64_t n_tiles = h->tile_row.empty() ? 0 : int64_t(h->tile_row.size()) - 1;
@@ -800,8 +741,6 @@ static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags,
     return ARROW_OK;
 }
 
-static uint32_t col_mask_of(const arrow_handle_s* h) { return h->col_classes ? kClassMask : 0xffffffffu; }
-
 static int sigma_of(int flags) {
     return ((flags & ARROW_RELU) ? kSigmaRelu : 0) | ((flags & ARROW_ROWNORM) ? kSigmaRowNorm : 0);
 }
@@ -815,8 +754,7 @@ static void launch_step(const arrow_handle_s* h, const Plan& p, const TX* cur, T
     for (int ch = 0; ch < p.chunks; ++ch) {
         const int koff = ch * p.kc;
         if (!h->seg_begin.empty()) {
-            SegArgs sa{d.seg_begin, d.seg_end, int64_t(h->seg_begin.size()), lcol, d.lval, cur, k, koff, p.kc, part,
-                       col_mask_of(h), p.hot_cls};
+            SegArgs sa{d.seg_begin, d.seg_end, int64_t(h->seg_begin.size()), lcol, d.lval, cur, k, koff, p.kc, part};
             const int64_t warps = int64_t(h->seg_begin.size());
             const int grid = int(std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, int64_t(d.sm_count) * 8)));
             cudaEvent_t e0 = pf.begin();
@@ -825,7 +763,7 @@ static void launch_step(const arrow_handle_s* h, const Plan& p, const TX* cur, T
         }
         const TileLayout L = tile_layout(h->tune.tile_rows, h->tune.tile_nnz);
         RowArgs ra{d.rowptr, col, d.val, d.tile_row, d.tile_ent, n_tiles, cur, nxt, k, koff, p.kc, scale_in, np,
-                   d.status, L.rp, L.col, L.buf, sigma, col_mask_of(h), p.hot_cls};
+                   d.status, L.rp, L.col, L.buf, sigma};
         const int smem = rows_smem_bytes(L, np ? (256 / T) * p.kc : 0);
         cudaEvent_t e0 = pf.begin();
         if (np) {
@@ -1253,7 +1191,7 @@ int arrow_set_tuning(arrow_handle h, const arrow_tuning* t) {
     if (!h || !t) { set_error("arrow_set_tuning: NULL argument"); return ARROW_EINVAL; }
     if (t->tile_rows < 32 || t->tile_rows > kMaxTileRows || t->tile_nnz < kMinTileNnz || t->tile_nnz > kMaxTileNnz ||
         t->ctas_per_sm < 1 || t->ctas_per_sm > ARROW_ROWS_MIN_BLOCKS || t->carveout < 0 || t->carveout > 100 ||
-        t->l2_hot_mb < 0 || t->l2_hot_mb > 1024 || t->fold_permute_in < 0 || t->fold_permute_in > 1) {
+        t->fold_permute_in < 0 || t->fold_permute_in > 1) {
         set_error("arrow_set_tuning: value out of range");
         return ARROW_EINVAL;
     }
@@ -1302,7 +1240,7 @@ int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t it
             const int per = rows_smem_bytes(L, (flags & ARROW_RESCALE) ? 256 * int(16 / dtype_size(x_dtype)) : 0) + 1024;
             if (ctas * per > 227 * 1024) break;
             const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);
-            arrow_tuning cand{sh[0], sh[1], ctas, pct, h->tune.l2_hot_mb, h->tune.fold_permute_in};
+            arrow_tuning cand{sh[0], sh[1], ctas, pct, h->tune.fold_permute_in};
             if ((rc = arrow_set_tuning(h, &cand))) break;
             if ((rc = arrow_spmm(h, X, k, iters, Y, x_dtype, flags, stream))) break;
             cudaEventRecord(e0, s);

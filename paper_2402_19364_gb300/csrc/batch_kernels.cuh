@@ -31,7 +31,6 @@ struct MatDesc {
     int64_t k;
     int32_t T;            // lanes per row = k / V
     int32_t flip;         // xor-ed into the launch parity (per-request ping-pong state)
-    uint32_t col_mask;    // strips the access-class bits of the device column indices
 };
 
 struct BatchArgs {
@@ -132,7 +131,7 @@ __global__ void __launch_bounds__(256, kBatchMinBlocks) arrow_batch_rows_kernel(
                 uint4 x[kBatchRound];
 #pragma unroll
                 for (int u = 0; u < kBatchRound; ++u)
-                    if (u < cnt) x[u] = ld_x(X + int64_t(uint32_t(scol[base + u]) & d.col_mask) * ldx);
+                    if (u < cnt) x[u] = ld_x(X + int64_t(scol[base + u]) * ldx);
 #pragma unroll
                 for (int u = 0; u < kBatchRound; ++u) {
                     if (u < cnt) {
@@ -174,8 +173,7 @@ __device__ __forceinline__ void batch_segment(const MatDesc& d, int64_t g, int p
     const TX* __restrict__ X = static_cast<const TX*>(par ? d.xb : d.xa) + tl * V;
     const int32_t s = __ldg(d.seg_begin + g), e = __ldg(d.seg_end + g);
     float acc[V];
-    segment_partial<TX, TV, T>(d.lcol, static_cast<const TV*>(d.lval), X, d.k, s, e, lane, acc,
-                               make_gather(d.col_mask, kNoHints));
+    segment_partial<TX, TV, T>(d.lcol, static_cast<const TV*>(d.lval), X, d.k, s, e, lane, acc);
 #pragma unroll
     for (int off = T; off < 32; off <<= 1)
 #pragma unroll

@@ -94,51 +94,6 @@ __device__ __forceinline__ void st_y(void* p, const uint4& v) {
     *reinterpret_cast<uint4*>(p) = v;
 #endif
 }
-// ------------------------------------------------------------------------------------
-// L2 residency of the X gathers
-// ------------------------------------------------------------------------------------
-// The device copies of the column indices carry, in bits 27..30, the access class of the X
-// row they name: min(15, bit length of the number of entries of A in that column), i.e.
-// how many gathers of that row one iteration makes (only when n < 2^27; otherwise the bits
-// are zero and the mask keeps all 31).  A launch marks the rows of class >= thr as
-// evict_last in L2 and the rest evict_first, so the rows read most often stay resident while
-// rows read a few times stream through (a power-law graph sends most of its gathers to a
-// small set of columns).  thr >= 16 turns the hints off (plain loads).
-constexpr int kClassShift = 27;
-constexpr uint32_t kClassMask = (1u << kClassShift) - 1u;
-constexpr int kNoHints = 16;
-
-struct Gather {
-    uint32_t mask;   // kClassMask when the indices carry classes, else all ones
-    int thr;         // classes >= thr are kept (evict_last); kNoHints: plain loads
-    uint64_t hot, cold;
-};
-__device__ __forceinline__ Gather make_gather(uint32_t mask, int thr) {
-    Gather g;
-    g.mask = mask;
-    g.thr = thr;
-    g.hot = g.cold = 0;
-    if (thr < kNoHints) {
-        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(g.hot));
-        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(g.cold));
-    }
-    return g;
-}
-__device__ __forceinline__ uint4 ld_x_pol(const void* p, uint64_t pol) {
-    uint4 r;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p), "l"(pol));
-    return r;
-}
-// The 16-byte slice of the X row named by the encoded column c (X already offset to the
-// lane's slice; ldx elements per row).
-template <typename TX>
-__device__ __forceinline__ uint4 gather_x(const TX* X, uint32_t c, int64_t ldx, const Gather& g) {
-    const TX* p = X + int64_t(c & g.mask) * ldx;
-    if (g.thr >= kNoHints) return ld_x(p);
-    return ld_x_pol(p, int(c >> kClassShift) >= g.thr ? g.hot : g.cold);
-}
-
 __device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
     int32_t r;
     asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(r) : "l"(p));
@@ -213,7 +168,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 template <typename TX, typename TV, int T, int U = 8>
 __device__ __forceinline__ void segment_partial(const int32_t* __restrict__ col, const TV* __restrict__ val,
                                                       const TX* __restrict__ X, int64_t ldx, int s, int e, int lane,
-                                                      float* acc, const Gather& gp) {
+                                                      float* acc) {
     using P = Pack<TX>;
     constexpr int V = P::V;
     constexpr int TPW = 32 / T;
@@ -230,7 +185,7 @@ __device__ __forceinline__ void segment_partial(const int32_t* __restrict__ col,
 #pragma unroll
         for (int u = 0; u < U; ++u) w[u] = val_to_float(ld_stream_val<TV>(val + j + u * TPW));
 #pragma unroll
-        for (int u = 0; u < U; ++u) x[u] = gather_x(X, uint32_t(c[u]), ldx, gp);
+        for (int u = 0; u < U; ++u) x[u] = ld_x(X + int64_t(c[u]) * ldx);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             float f[V];
@@ -243,7 +198,7 @@ __device__ __forceinline__ void segment_partial(const int32_t* __restrict__ col,
         const int32_t c = ld_stream_i32(col + j);
         const float w = val_to_float(ld_stream_val<TV>(val + j));
         float f[V];
-        P::to_float(gather_x(X, uint32_t(c), ldx, gp), f);
+        P::to_float(ld_x(X + int64_t(c) * ldx), f);
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = fmaf(w, f[v], acc[v]);
     }

@@ -177,26 +177,27 @@ def test_sigma_rownorm_needs_one_team_per_row(arrow):
 
 
 @pytest.mark.parametrize("dt,k,rescale", [("f32", 16, True), ("bf16", 128, False), ("f16", 32, False)])
-def test_fold_and_l2_hints_keep_the_bits(arrow, dt, k, rescale):
-    """The permute-in folded into the first iteration and the L2 residency hints change where
-    data comes from, not the arithmetic: results are bit-identical to the plain path, and
-    match the oracle.  A 1 MB hot budget makes the hints engage on a small power-law matrix."""
+def test_folded_permute_in_keeps_the_bits(arrow, dt, k, rescale):
+    """The permute-in folded into the first iteration changes where the first step reads X
+    from, not the arithmetic: results are bit-identical to the plain path and match the
+    oracle; the caller's X is only read, and X and Y may still alias."""
     A = w.rmat_gcn(13, 16, seed=5)
     X = w.features(A.n, k, seed=3)
     M = arrow.ArrowMatrix(A, 128, value_dtype=dt, long_row=32, segment=128)
     Xd = torch.from_numpy(X).to("cuda", TORCH_DT[dt])
     t = M.tuning
-    M.set_tuning(t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"], 0, 0)
+    M.set_tuning(t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"], 0)
     ref = M.spmm(Xd, 6, rescale=rescale)
-    for hot_mb, fold in ((1, 0), (0, 1), (1, 1), (64, 1)):
-        M.set_tuning(t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"], hot_mb, fold)
+    M.set_tuning(t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"], 1)
+    for iters in (6, 1):
         Xa = Xd.clone()
-        Y = M.spmm(Xa, 6, rescale=rescale)
+        Y = M.spmm(Xa, iters, rescale=rescale)
         torch.cuda.synchronize()
-        assert torch.equal(Y, ref), (hot_mb, fold)
-        assert torch.equal(Xa, Xd)                               # the caller's X is only read
-        M.spmm(Xa, 6, rescale=rescale, out=Xa)                  # X and Y may alias with the fold
-        assert torch.equal(Xa, ref)
+        assert torch.equal(Xa, Xd)                              # the caller's X is only read
+        if iters == 6:
+            assert torch.equal(Y, ref)
+        M.spmm(Xa, iters, rescale=rescale, out=Xa)             # X and Y may alias with the fold
+        assert torch.equal(Xa, Y)
     R = S.iterate(A, X, 6, rescale=rescale)
     Yn = ref.float().cpu().numpy().astype(np.float64)
     assert (err_inf(Yn, R) <= 6e-5) if dt == "f32" else (err_2(Yn, R) <= 2e-2)
