@@ -62,12 +62,19 @@ typedef struct {
 
 /* ---- decomposition options ------------------------------------------------------- */
 #define ARROW_HOST_ONLY 0x1   /* opts.flags: build on the host, do not touch a GPU */
+/* opts.flags: run the data-parallel steps of LA-Decompose on the GPU (opts.device, or the
+ * current one): per level the degrees, the edges of G_i' with their random keys, the minimum
+ * spanning forest (Boruvka; Section 4.3) and the split of the entries by the arrow shape
+ * (steps 3-4 of Section 4.1).  The head choice and the tree layout (Section 4.4) stay on the
+ * host.  The result is the host path's decomposition, bit for bit.  Needs device memory of
+ * about 40 bytes per entry of the symmetric pattern while it runs.  Not with ARROW_HOST_ONLY. */
+#define ARROW_DEVICE_DECOMPOSE 0x2
 
 typedef struct {
     uint64_t seed;        /* seed of the random edge weights (Section 4.3 step 1)           */
     int32_t  value_dtype; /* arrow_dtype the device stores A's values in (RNE from float64) */
     int32_t  predicate;   /* ARROW_PRED_BLOCK (default) or ARROW_PRED_BAND                  */
-    int32_t  flags;       /* ARROW_HOST_ONLY or 0                                            */
+    int32_t  flags;       /* ARROW_HOST_ONLY, ARROW_DEVICE_DECOMPOSE or 0                    */
     int32_t  nthreads;    /* host threads for the decomposition; 0 = all hardware threads   */
     int32_t  max_levels;  /* cap on the order l of the decomposition; 0 = 254               */
     int32_t  long_row;    /* rows with more entries than this are split; 0 = default (64)   */

@@ -79,7 +79,7 @@ class ArrowMatrix:
 
     def __init__(self, A, b: int, *, seed: int = 0, value_dtype="f32", predicate: str = "block",
                  host_only: bool = False, nthreads: int = 0, max_levels: int = 0, long_row: int = 0,
-                 segment: int = 0, device: int = -1):
+                 segment: int = 0, device: int = -1, device_decompose: bool = False):
         L = _native.lib()
         self._h = ctypes.c_void_p()
         csr, _keep = _csr(A)
@@ -88,7 +88,7 @@ class ArrowMatrix:
         o.seed = seed
         o.value_dtype = dtype_code(value_dtype)
         o.predicate = {"block": ARROW_PRED_BLOCK, "band": ARROW_PRED_BAND}[predicate]
-        o.flags = ARROW_HOST_ONLY if host_only else 0
+        o.flags = (ARROW_HOST_ONLY if host_only else 0) | (_native.ARROW_DEVICE_DECOMPOSE if device_decompose else 0)
         o.nthreads = nthreads
         o.max_levels = max_levels
         o.long_row = long_row

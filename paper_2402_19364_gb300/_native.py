@@ -18,6 +18,7 @@ ERROR_NAMES = {ARROW_EINVAL: "EINVAL", ARROW_ENOMEM: "ENOMEM", ARROW_ECUDA: "ECU
 ARROW_F32, ARROW_BF16, ARROW_F16 = 0, 1, 2
 ARROW_PRED_BLOCK, ARROW_PRED_BAND = 0, 1
 ARROW_HOST_ONLY = 0x1
+ARROW_DEVICE_DECOMPOSE = 0x2
 ARROW_RESCALE = 0x1
 ARROW_PROFILE = 0x2
 ARROW_GRAPH = 0x4

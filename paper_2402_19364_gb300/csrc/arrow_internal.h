@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/arrow.h"
@@ -113,6 +114,18 @@ struct arrow_handle_s {
 };
 
 namespace arrow {
+// Steps of LA-Decompose on the current GPU (decompose_device.cu), used by decompose_host
+// with ARROW_DEVICE_DECOMPOSE: the remaining entries (r, c, index) live on the device.
+struct DeviceDecomp;
+int dd_begin(DeviceDecomp** out, int64_t n, int64_t snnz, const void* act);   // act: snnz (r, c, s) int32 triples
+int64_t dd_remaining(const DeviceDecomp* d);
+int dd_degrees(DeviceDecomp* d, int32_t* deg, uint8_t* touched);               // host arrays of n
+int dd_forest(DeviceDecomp* d, const uint8_t* is_head, uint64_t salt, std::vector<int32_t>& comp,
+              std::vector<std::pair<int32_t, int32_t>>& forest);
+int dd_split(DeviceDecomp* d, const int32_t* perm, int64_t b, bool band, int level);
+int dd_levels(DeviceDecomp* d, uint8_t* lvl);                                 // host array of snnz
+void dd_free(DeviceDecomp* d);
+
 // Host decomposition (decompose.cpp).  Fills levels, entry_level and the fused row program.
 int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow_opts& o);
 // (Re)build the row tiles of the fused row program (decompose.cpp).

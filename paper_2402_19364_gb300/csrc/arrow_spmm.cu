@@ -998,15 +998,31 @@ int arrow_decompose(const arrow_csr* A, int64_t b, const arrow_opts* o, arrow_ha
     *out = nullptr;
     arrow_opts opts;
     if (o) opts = *o; else arrow_opts_default(&opts);
+    if ((opts.flags & ARROW_DEVICE_DECOMPOSE) && (opts.flags & ARROW_HOST_ONLY)) {
+        set_error("arrow_decompose: ARROW_DEVICE_DECOMPOSE needs a GPU, ARROW_HOST_ONLY forbids one");
+        return ARROW_EINVAL;
+    }
+    // the device steps run on opts.device (or the current device); the caller's current
+    // device is given back afterwards
+    int prev = -1;
+    const bool switch_dev = (opts.flags & ARROW_DEVICE_DECOMPOSE) && opts.device >= 0;
+    if (switch_dev) {
+        ACK(cudaGetDevice(&prev));
+        if (prev != opts.device) ACK(cudaSetDevice(opts.device));
+    }
     arrow_handle_s* h = nullptr;
+    int drc = ARROW_OK;
     try {
         h = new arrow_handle_s();
-        int rc = decompose_host(h, A, b, opts);
-        if (rc != ARROW_OK) { delete h; return rc; }
+        drc = decompose_host(h, A, b, opts);
     } catch (const std::bad_alloc&) {
-        delete h;
         set_error("arrow_decompose: host allocation failed");
-        return ARROW_ENOMEM;
+        drc = ARROW_ENOMEM;
+    }
+    if (switch_dev && prev != opts.device) cudaSetDevice(prev);
+    if (drc != ARROW_OK) {
+        delete h;
+        return drc;
     }
     if (!(opts.flags & ARROW_HOST_ONLY)) {
         int rc = arrow_upload(h);

@@ -658,8 +658,21 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
     const bool band = o.predicate == ARROW_PRED_BAND;
     std::vector<int32_t> deg(n);
     std::vector<uint8_t> is_head(n), touched(n);
+    // ARROW_DEVICE_DECOMPOSE: the degrees, the edges of G_i' with their keys, the spanning
+    // forest and the split run on the current GPU (decompose_device.cu); the head and the tree
+    // layout stay here.  The remaining entries then live on the device.
+    const bool on_dev = (o.flags & ARROW_DEVICE_DECOMPOSE) != 0;
+    struct DdHold {
+        DeviceDecomp* d = nullptr;
+        ~DdHold() { dd_free(d); }
+    } dd;
+    if (on_dev) {
+        int drc = dd_begin(&dd.d, n, S.nnz, act.data());
+        if (drc != ARROW_OK) return drc;
+        uvec<Ent>().swap(act);
+    }
     int level = 0;
-    while (!act.empty()) {
+    while (on_dev ? dd_remaining(dd.d) > 0 : !act.empty()) {
         if (level == fail_level) throw std::bad_alloc();
         if (level >= max_levels) {
             set_error("arrow_decompose: more than max_levels levels");
@@ -667,9 +680,13 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
         }
         std::fill(deg.begin(), deg.end(), 0);
         std::fill(touched.begin(), touched.end(), 0);
+        if (on_dev) {
+            int drc = dd_degrees(dd.d, deg.data(), touched.data());
+            if (drc != ARROW_OK) return drc;
+        }
         // act stays sorted by row (it is filtered in order), so a chunk counts each row's
         // off-diagonal entries in one run; only the rows cut by a chunk boundary are shared
-        pfor(int64_t(act.size()), [&](int64_t bb, int64_t e, int) {
+        if (!on_dev) pfor(int64_t(act.size()), [&](int64_t bb, int64_t e, int) {
             for (int64_t i = bb; i < e;) {
                 const int32_t r = act[i].r;
                 int32_t cnt = 0;
@@ -689,6 +706,12 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
 
         // edges of G_i' = G_i[V \ V^h], keyed by the level's random weights
         const uint64_t salt = splitmix64(o.seed + uint64_t(level));
+        std::vector<int32_t> comp;
+        std::vector<std::pair<int32_t, int32_t>> forest;
+        if (on_dev) {
+            int drc = dd_forest(dd.d, is_head.data(), salt, comp, forest);
+            if (drc != ARROW_OK) return drc;
+        } else {
         uvec<int32_t> eu, ev;
         uvec<uint64_t> ew;
         {
@@ -705,15 +728,21 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
                 }
             });
         }
-        std::vector<int32_t> comp;
-        std::vector<std::pair<int32_t, int32_t>> forest;
         boruvka(n, std::move(eu), std::move(ev), std::move(ew), comp, forest);
+        }
         Level L;
         std::vector<int32_t> iperm;
         arrange(n, head, is_head, touched, comp, forest, L.perm, iperm);
 
         // steps 3-4: entries inside the arrow shape go to B_i, the rest stays
         const int32_t* perm = L.perm.data();
+        if (on_dev) {
+            int drc = dd_split(dd.d, perm, b, band, level);
+            if (drc != ARROW_OK) return drc;
+            h->levels.push_back(std::move(L));
+            ++level;
+            continue;
+        }
         uvec<Ent> rest;
         pfilter(int64_t(act.size()), rest,
                 [&](int64_t i) {
@@ -727,6 +756,10 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
         act.swap(rest);
         h->levels.push_back(std::move(L));
         ++level;
+    }
+    if (on_dev) {
+        int drc = dd_levels(dd.d, lvlS.data());
+        if (drc != ARROW_OK) return drc;
     }
     // level of every entry of A, per-level nnz and active rows
     h->entry_level.resize(nnz);
