@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp32", action="store_true", help="skip the FP32 arm of a 16-bit workload")
+    p.add_argument("--no-device-decompose", action="store_true",
+                   help="skip timing the decomposition with its steps on the GPU")
     p.add_argument("--no-sub", action="store_true", help="default workload only: skip the other configurations' records")
     p.add_argument("--sub", default="grid2d,rmat,batch,serve", help="which other configurations to attach")
     p.add_argument("--tuning", default="", help="tile_rows,tile_nnz,ctas_per_sm,carveout[,fold_permute_in]: fixed tuning "
@@ -768,6 +770,19 @@ def main():
     M = arrow.ArrowMatrix(A, spec["b"], value_dtype=dt_name, device=local)
     t_dec = time.perf_counter() - t0
     st = M.stats()
+    # the same decomposition with its data-parallel steps on the GPU (ARROW_DEVICE_DECOMPOSE):
+    # timed, and checked equal to the host one (first and last level permutations)
+    dev_dec = None
+    if not a.no_device_decompose:
+        t0 = time.perf_counter()
+        Md = arrow.ArrowMatrix(A, spec["b"], value_dtype=dt_name, device=local, host_only=False,
+                               device_decompose=True)
+        t_dd = time.perf_counter() - t0
+        same = Md.num_levels == M.num_levels and all(
+            np.array_equal(Md.level_perm(i), M.level_perm(i)) for i in {0, M.num_levels - 1} if M.num_levels)
+        dev_dec = {"decompose_and_upload": t_dd, "decompose": Md.stats()["decompose_seconds"],
+                   "same_permutations_as_host": bool(same)}
+        Md.close()
     levels = [M.level_info(i) for i in range(M.num_levels)]
     import workloads as w
     Xh = torch.from_numpy(w.features(A.n, k, seed=spec["seed_x"] + 1000 * rank)).to(tdt)
@@ -812,7 +827,7 @@ def main():
            "roofline": roofline, "gpu_launches": tm["launches"], "clocks": clk,
            "kernel_ms": {c: v / a.steps for c, v in tm["kernel_ms"].items()},
            "prep_s": {"generate": t_gen, "decompose_and_upload": t_dec, "decompose_host": st["decompose_seconds"],
-                      "autotune": t_tune}}
+                      "autotune": t_tune, "device_decompose": dev_dec}}
     if spec["name"] == "grid2d":
         out["us_per_iter"] = ms_step / iters * 1e3
 

@@ -90,8 +90,8 @@ int arrow_opts_default(arrow_opts* o);
 /* ---- launch tuning -------------------------------------------------------------------- */
 /* How the fused row program is cut and launched (not in the paper; a property of this GPU
  * path): rows per tile, entries per tile (>= 1024, so every unsplit row fits), resident CTAs
- * per SM of the persistent rows kernel (1..4; with ARROW_RESCALE at most 3 are used, the
- * register bound of that variant), the shared-memory carveout in percent, and
+ * per SM of the persistent rows kernel (1..4, as far as shared memory allows), the
+ * shared-memory carveout in percent, and
  * fold_permute_in = 1, which makes the first iteration gather straight from the caller's X
  * through a second copy of the column indices in vertex ids (4 bytes per entry of device
  * memory, set up when the setting is applied) instead of permuting X into pi_0 order first.

@@ -304,6 +304,7 @@ int arrow_batch_autotune(arrow_batch B, const void* const* X, void* const* Y, co
         for (int ctas = 2; ctas <= kBatchMinBlocks; ++ctas) {
             const TileLayout L = tile_layout(sh[0], sh[1]);
             const int per = batch_smem_bytes(L) + 1024;
+            if (ctas * per > 227 * 1024) break;             // would not be resident together
             const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);
             arrow_tuning cand{sh[0], sh[1], ctas, pct, B->hs[0]->tune.fold_permute_in};
             if ((rc = apply(cand))) break;

@@ -39,14 +39,15 @@ namespace arrow {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
-// CTAs of the rows kernel that fit an SM by registers (launch bounds): 4 for the plain
-// product, 3 with the FP64 rescale (its norm sums need more registers; at 4 it spills).
-// arrow_tuning's ctas_per_sm is capped by the variant's bound at launch.
+// CTAs of the rows kernel that fit an SM by registers (launch bounds, 64 registers): 4 for
+// both variants (the row gathers in exact-size rounds left the FP64-rescale variant room to
+// fit without spilling).  arrow_tuning's ctas_per_sm is capped by the variant's bound at
+// launch, and by shared memory in the autotuner.
 #ifndef ARROW_ROWS_MIN_BLOCKS
 #define ARROW_ROWS_MIN_BLOCKS 4
 #endif
 #ifndef ARROW_ROWS_MIN_BLOCKS_RESCALE
-#define ARROW_ROWS_MIN_BLOCKS_RESCALE 3
+#define ARROW_ROWS_MIN_BLOCKS_RESCALE 4
 #endif
 
 // ------------------------------------------------------------------------------------
@@ -182,23 +183,7 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
             float acc[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.f;
-            for (int base = s; base < e; base += 8) {
-                const int cnt = e - base;
-                uint4 x[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (u < cnt) x[u] = ld_x(X + int64_t(scol[base + u]) * a.ldx);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (u < cnt) {
-                        const float w = val_to_float(sval[base + u]);
-                        float f[V];
-                        P::to_float(x[u], f);
-#pragma unroll
-                        for (int v = 0; v < V; ++v) acc[v] = fmaf(w, f[v], acc[v]);
-                    }
-                }
-            }
+            gather_row<TX, TV>(scol, sval, s, e, X, a.ldx, acc);
             if (RESCALE) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v] *= scl[v];

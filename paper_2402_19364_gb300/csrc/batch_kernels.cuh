@@ -57,13 +57,9 @@ inline int batch_smem_bytes(const TileLayout& L) { return 128 + kStages * L.buf;
 
 // Rows of every matrix's tiles (the fused arrow-row kernel of arrow_spmm with a per-tile
 // matrix descriptor and a run-time team width); same tile pipeline without block barriers.
-// Entries per gather round of a row (all of a round's gathers are in flight together) and the
-// resident CTAs per SM that the register use allows.
-#ifndef ARROW_BATCH_ROUND
-#define ARROW_BATCH_ROUND 8
-#endif
-constexpr int kBatchRound = ARROW_BATCH_ROUND;
-constexpr int kBatchMinBlocks = kBatchRound > 8 ? 2 : 3;
+// Resident CTAs per SM that the register use of the batched rows kernel allows (rows are
+// gathered in rounds of 8, see gather_row).
+constexpr int kBatchMinBlocks = 4;
 
 template <typename TX, typename TV>
 __global__ void __launch_bounds__(256, kBatchMinBlocks) arrow_batch_rows_kernel(BatchArgs a) {
@@ -126,23 +122,7 @@ __global__ void __launch_bounds__(256, kBatchMinBlocks) arrow_batch_rows_kernel(
             float acc[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.f;
-            for (int base = s; base < e; base += kBatchRound) {
-                const int cnt = e - base;
-                uint4 x[kBatchRound];
-#pragma unroll
-                for (int u = 0; u < kBatchRound; ++u)
-                    if (u < cnt) x[u] = ld_x(X + int64_t(scol[base + u]) * ldx);
-#pragma unroll
-                for (int u = 0; u < kBatchRound; ++u) {
-                    if (u < cnt) {
-                        const float wv = val_to_float(sval[base + u]);
-                        float f[V];
-                        P::to_float(x[u], f);
-#pragma unroll
-                        for (int v = 0; v < V; ++v) acc[v] = fmaf(wv, f[v], acc[v]);
-                    }
-                }
-            }
+            gather_row<TX, TV>(scol, sval, s, e, X, ldx, acc);
             *reinterpret_cast<uint4*>(Y + int64_t(r0 + j) * ldx) = P::from_float(acc);
         }
         __syncwarp();

@@ -204,6 +204,47 @@ __device__ __forceinline__ void segment_partial(const int32_t* __restrict__ col,
     }
 }
 
+// One gather round of a row staged in shared memory: the R entries base..base+R-1 (column
+// and value from shared memory), their 16-byte X gathers issued together, then accumulated
+// into acc in entry order.
+template <int R, typename TX, typename TV>
+__device__ __forceinline__ void gather_round(const int32_t* scol, const TV* sval, int base, const TX* X, int64_t ldx,
+                                             float* acc) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    uint4 x[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) x[u] = ld_x(X + int64_t(scol[base + u]) * ldx);
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const float w = val_to_float(sval[base + u]);
+        float f[V];
+        P::to_float(x[u], f);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = fmaf(w, f[v], acc[v]);
+    }
+}
+
+// All entries [s, e) of a staged row in entry order: full rounds of 8 gathers, then one round
+// of exactly the remaining 1..7 (a round of 8 with the unused slots predicated off would
+// still issue their instructions: a 9-entry row spent 16 slots' worth).
+template <typename TX, typename TV>
+__device__ __forceinline__ void gather_row(const int32_t* scol, const TV* sval, int s, int e, const TX* X, int64_t ldx,
+                                           float* acc) {
+    int base = s;
+    for (; base + 8 <= e; base += 8) gather_round<8>(scol, sval, base, X, ldx, acc);
+    switch (e - base) {
+        case 7: gather_round<7>(scol, sval, base, X, ldx, acc); break;
+        case 6: gather_round<6>(scol, sval, base, X, ldx, acc); break;
+        case 5: gather_round<5>(scol, sval, base, X, ldx, acc); break;
+        case 4: gather_round<4>(scol, sval, base, X, ldx, acc); break;
+        case 3: gather_round<3>(scol, sval, base, X, ldx, acc); break;
+        case 2: gather_round<2>(scol, sval, base, X, ldx, acc); break;
+        case 1: gather_round<1>(scol, sval, base, X, ldx, acc); break;
+        default: break;
+    }
+}
+
 // Tile pipeline state at the start of dynamic shared memory (128 bytes): one "full"
 // mbarrier per staging buffer (completed by the buffer's bulk copies), the number of warps
 // done with the buffer's current use, the buffer's issued uses, and a small header.
