@@ -8,7 +8,7 @@ Default workload (one step = one arrow_spmm call = the whole hot path once):
 Inputs (X 4.1 GB, A 3.6 GB) are larger than the 129 MB L2, so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload grid3d|grid2d|rmat|batch|serve] [--size S] [--iters T] [--k K]
+                  [--workload grid3d|grid2d|rmat|batch|serve|predicates] [--size S] [--iters T] [--k K]
                   [--dtype f32|bf16] [--count M] [--tuning R,E,C,P] [--no-e2e] [--no-cpu] [--no-cusparse]
 
 The line carries the device-timed value, the rows kernel's roofline, per-step min/mean/max,
@@ -38,7 +38,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "arrow-SpMM iters/s & HBM GB/s (% of peak) vs plain FP32/cuSPARSE; serve p50/p99"
-KERNEL_SRC = os.path.join(ROOT, "paper_2402_19364_gb300", "csrc", "arrow_spmm.cu")
+# the sources the single-matrix kernels are compiled from (the traffic record is tied to them)
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2402_19364_gb300", "csrc", f) for f in ("arrow_spmm.cu", "device_common.cuh")]
 
 
 def parse():
@@ -47,7 +48,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="grid3d", choices=["grid3d", "grid2d", "rmat", "batch", "serve"])
+    p.add_argument("--workload", default="grid3d", choices=["grid3d", "grid2d", "rmat", "batch", "serve", "predicates"])
     p.add_argument("--count", type=int, default=0, help="matrices of the batch workload (0 = 512)")
     p.add_argument("--size", type=int, default=0, help="grid side / R-MAT scale (0 = workload default)")
     p.add_argument("--iters", type=int, default=0)
@@ -60,7 +61,7 @@ def parse():
     p.add_argument("--no-device-decompose", action="store_true",
                    help="skip timing the decomposition with its steps on the GPU")
     p.add_argument("--no-sub", action="store_true", help="default workload only: skip the other configurations' records")
-    p.add_argument("--sub", default="grid2d,rmat,batch,serve", help="which other configurations to attach")
+    p.add_argument("--sub", default="grid2d,rmat,batch,serve,predicates", help="which other configurations to attach")
     p.add_argument("--tuning", default="", help="tile_rows,tile_nnz,ctas_per_sm,carveout[,fold_permute_in]: fixed tuning "
                    "instead of autotuning (keeps a profiler's launch list short)")
     return p.parse_args()
@@ -129,22 +130,39 @@ def workload_key(spec) -> str:
     return f"{spec['name']} N={spec['N']} k={spec['k']} {spec['dtype']} rescale={int(spec['rescale'])}"
 
 
+def kernel_source_digest() -> str:
+    """First 16 hex digits of the SHA-256 of the kernel sources, concatenated in order."""
+    h = hashlib.sha256()
+    for path in KERNEL_SRCS:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(workload: str):
-    """DRAM bytes per rows-kernel launch from the committed ncu summary, if it was taken on
-    the current kernel source and on this workload (profiles/arrow_rows_traffic.txt); else None."""
+    """DRAM bytes per iteration of the rows (+ split-row) kernels from the committed ncu summary
+    (profiles/arrow_rows_traffic.txt: one block per workload, each starting with its
+    'workload:' line), if the block for this workload was taken on the current kernel sources;
+    else None."""
     path = os.path.join(ROOT, "profiles", "arrow_rows_traffic.txt")
     try:
-        with open(KERNEL_SRC, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()[:16]
-        kv = {}
+        digest = kernel_source_digest()
+        blocks, kv = [], None
         with open(path) as f:
             for line in f:
-                if ":" in line and not line.startswith("#"):
-                    k, v = line.split(":", 1)
-                    kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_sha256_16") != digest or kv.get("workload") != workload:
-            return None
-        return kv
+                if ":" not in line or line.startswith("#"):
+                    continue
+                k, v = line.split(":", 1)
+                k, v = k.strip(), v.strip()
+                if k == "workload":
+                    kv = {}
+                    blocks.append(kv)
+                if kv is not None:
+                    kv[k] = v
+        for kv in blocks:
+            if kv.get("workload") == workload and kv.get("kernel_source_sha256_16") == digest:
+                return kv
+        return None
     except Exception:
         return None
 
@@ -718,6 +736,7 @@ SUBRECORDS = [
     ("rmat", ["--workload", "rmat", "--steps", "5", "--warmup", "3"]),
     ("batch", ["--workload", "batch", "--steps", "5", "--warmup", "3"]),
     ("serve", ["--workload", "serve"]),
+    ("predicates", ["--workload", "predicates", "--steps", "3"]),
 ]
 
 
@@ -742,8 +761,58 @@ def run_subrecords(keys, timeout_s=1800):
     return recs
 
 
+def run_predicates(a):
+    """The two arrow shapes on the GPU (Section 1's band |p - q| <= b against the block-diagonal
+    tiles of Section 3.1): levels, non-zero b x b tiles, algorithmic bytes per iteration and the
+    measured time of the same product on a 3D 200^3 grid (k = 16 FP32, 20 iterations with the
+    rescale) and an R-MAT scale 21 graph (k = 128 BF16, 8 iterations)."""
+    import torch
+    import workloads as w
+    from paper_2402_19364_gb300 import build as _build
+    _build.build()
+    import paper_2402_19364_gb300 as arrow
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    cases = [("3D 200^3 grid, b = 4096, k = 16 FP32, 20 iterations with the rescale", w.grid3d(200, seed=3), 4096, 16,
+              "f32", 20, True),
+             ("R-MAT scale 21 GCN, b = 8192, k = 128 BF16, 8 iterations", w.rmat_gcn(21, 16, seed=5), 8192, 128, "bf16",
+              8, False)]
+    out = {"metric": "arrow-SpMM band vs block predicate (levels, tiles, bytes, time)", "data": "synthetic",
+           "n_gpus": 1, "cases": []}
+    for desc, A, b, k, dt, iters, rs in cases:
+        X = torch.from_numpy(w.features(A.n, k, seed=4)).cuda().to({"f32": torch.float32, "bf16": torch.bfloat16}[dt])
+        rec = {"workload": desc, "n": A.n, "nnz": A.nnz}
+        ref = None
+        for pred in ("block", "band"):
+            M = arrow.ArrowMatrix(A, b, value_dtype=dt, predicate=pred)
+            M.autotune(X, iters, rescale=rs)
+            Y = torch.empty_like(X)
+            tm = time_calls(arrow, M, X, Y, iters, rs, max(3, a.steps), 3, None, stream)
+            rep = M.structure_report()
+            ab = M.algorithmic_bytes_per_iter(k, dt)
+            rec[pred] = {"levels": M.num_levels, "tiles": rep["tiles"], "level0_nnz_share": rep["levels"][0]["nnz_share"],
+                         "algorithmic_bytes_per_iter": ab["total"],
+                         "ms_per_iter": tm["ms_total"] / max(3, a.steps) / iters,
+                         "rows_segments_ms_per_iter": (tm["kernel_ms"]["rows"] + tm["kernel_ms"]["segments"])
+                         / max(1, tm["rows_launches"])}
+            Yf = Y.float()
+            if ref is None:
+                ref = Yf
+            else:
+                rec["max_normwise_diff_band_vs_block"] = float(
+                    (torch.linalg.vector_norm(Yf - ref, dim=0) / torch.linalg.vector_norm(ref, dim=0)).max())
+            M.close()
+        out["cases"].append(rec)
+        del X, ref
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
+    if a.workload == "predicates":
+        run_predicates(a)
+        return
     if a.workload == "batch":
         run_batch(a)
         return

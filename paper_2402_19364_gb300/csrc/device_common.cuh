@@ -225,9 +225,34 @@ __device__ __forceinline__ void gather_round(const int32_t* scol, const TV* sval
     }
 }
 
+// The same round when the row has only cnt (< R) entries left: the slots past cnt are
+// predicated off.
+template <int R, typename TX, typename TV>
+__device__ __forceinline__ void gather_round_upto(const int32_t* scol, const TV* sval, int base, int cnt, const TX* X,
+                                                  int64_t ldx, float* acc) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    uint4 x[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u)
+        if (u < cnt) x[u] = ld_x(X + int64_t(scol[base + u]) * ldx);
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        if (u < cnt) {
+            const float w = val_to_float(sval[base + u]);
+            float f[V];
+            P::to_float(x[u], f);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = fmaf(w, f[v], acc[v]);
+        }
+    }
+}
+
 // All entries [s, e) of a staged row in entry order: full rounds of 8 gathers, then one round
-// of exactly the remaining 1..7 (a round of 8 with the unused slots predicated off would
-// still issue their instructions: a 9-entry row spent 16 slots' worth).
+// of exactly the remaining 1..7.  A round of 8 with the unused slots predicated off would
+// still issue their instructions (a 9-entry row spent 16 slots); the exact round costs a
+// divergent branch when the teams of a warp have different remainders, which is cheap when a
+// warp holds few teams (wide rows) and costly when it holds many (see gather_row_pred).
 template <typename TX, typename TV>
 __device__ __forceinline__ void gather_row(const int32_t* scol, const TV* sval, int s, int e, const TX* X, int64_t ldx,
                                            float* acc) {
@@ -243,6 +268,14 @@ __device__ __forceinline__ void gather_row(const int32_t* scol, const TV* sval, 
         case 1: gather_round<1>(scol, sval, base, X, ldx, acc); break;
         default: break;
     }
+}
+
+// The same sum in rounds of 8 whose slots past the row's end are predicated off: one code
+// path for all the teams of a warp, whatever their row lengths.
+template <typename TX, typename TV>
+__device__ __forceinline__ void gather_row_pred(const int32_t* scol, const TV* sval, int s, int e, const TX* X,
+                                                int64_t ldx, float* acc) {
+    for (int base = s; base < e; base += 8) gather_round_upto<8>(scol, sval, base, e - base, X, ldx, acc);
 }
 
 // Tile pipeline state at the start of dynamic shared memory (128 bytes): one "full"

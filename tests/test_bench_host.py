@@ -26,8 +26,7 @@ def test_default_workload_is_the_400_cubed_grid():
 def test_traffic_record_matches_source_and_workload():
     spec = bench.workload_spec(_args())
     tr = bench.kernel_traffic(bench.workload_key(spec))
-    with open(bench.KERNEL_SRC, "rb") as f:
-        digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    digest = bench.kernel_source_digest()
     if tr is None:
         pytest.skip("traffic record taken on another kernel source")      # reported as null then
     assert tr["kernel_source_sha256_16"] == digest
@@ -37,15 +36,31 @@ def test_traffic_record_matches_source_and_workload():
                                  float(tr["dram_bytes_write_per_launch_full_size"]), rel=1e-6)
     assert 0.5 < dram / alg < 1.5
     # any other workload (or size) gets no traffic figure
-    for other in (_args(workload="rmat"), _args(size=200), _args(k=32)):
+    for other in (_args(size=200), _args(k=32), _args(workload="grid2d")):
         assert bench.kernel_traffic(bench.workload_key(bench.workload_spec(other))) is None
 
 
 def test_traffic_guard_rejects_a_changed_source(tmp_path, monkeypatch):
     src = tmp_path / "k.cu"
     src.write_text("// another kernel\n")
-    monkeypatch.setattr(bench, "KERNEL_SRC", str(src))
+    monkeypatch.setattr(bench, "KERNEL_SRCS", [str(src)])
     assert bench.kernel_traffic("grid3d N=400 k=16 f32 rescale=1") is None
+    assert bench.kernel_traffic("rmat N=23 k=128 bf16 rescale=0") is None
+
+
+def test_traffic_record_blocks_are_parsed_per_workload(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    d = bench.kernel_source_digest()
+    (prof / "arrow_rows_traffic.txt").write_text(
+        "# header\nworkload: A\nkernel_source_sha256_16: %s\ndram_bytes_per_launch_full_size: 1\n"
+        "workload: B\nkernel_source_sha256_16: 0000\ndram_bytes_per_launch_full_size: 2\n"
+        "workload: C\nkernel_source_sha256_16: %s\ndram_bytes_per_launch_full_size: 3\n" % (d, d))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_traffic("A")["dram_bytes_per_launch_full_size"] == "1"
+    assert bench.kernel_traffic("B") is None                          # taken on another source
+    assert bench.kernel_traffic("C")["dram_bytes_per_launch_full_size"] == "3"
+    assert bench.kernel_traffic("D") is None
 
 
 def test_fixed_tuning_parse():

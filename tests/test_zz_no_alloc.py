@@ -58,6 +58,32 @@ def test_static_scratch_matches_arrow_spmm(arrow, rescale):
             assert _rel_inf(Y, ref) <= 1e-5 * iters
 
 
+def test_static_scratch_allocates_nothing(arrow):
+    """After a first call (which looks the array's address up), further calls leave the
+    device's free memory exactly as it was: the scratch is the library's fixed array."""
+    from paper_2402_19364_gb300 import _native
+    L = _native.lib()
+    A = w.rmat_gcn(12, 16, seed=5)
+    M = arrow.ArrowMatrix(A, 128, long_row=16, segment=64)
+    X = torch.from_numpy(w.features(A.n, 32, seed=1)).cuda()
+    Y = torch.empty_like(X)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        _native.check(L.arrow_spmm_static(M._h, ctypes.c_void_p(X.data_ptr()), 32, 4, ctypes.c_void_p(Y.data_ptr()),
+                                          _native.ARROW_F32, _native.ARROW_RESCALE,
+                                          ctypes.c_void_p(stream.cuda_stream)))
+
+    call()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_static_scratch_refuses_large_problems(arrow):
     from paper_2402_19364_gb300 import _native
     L = _native.lib()
