@@ -49,6 +49,11 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 #ifndef ARROW_ROWS_MIN_BLOCKS_RESCALE
 #define ARROW_ROWS_MIN_BLOCKS_RESCALE 4
 #endif
+// 1: a row's last round has exactly its remaining entries (gather_row); 0: rounds of 8 with
+// the slots past the row's end predicated off (gather_row_pred).
+#ifndef ARROW_ROWS_EXACT
+#define ARROW_ROWS_EXACT 1
+#endif
 
 // ------------------------------------------------------------------------------------
 // kernels
@@ -183,7 +188,11 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
             float acc[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.f;
+#if ARROW_ROWS_EXACT
             gather_row<TX, TV>(scol, sval, s, e, X, a.ldx, acc);
+#else
+            gather_row_pred<TX, TV>(scol, sval, s, e, X, a.ldx, acc);
+#endif
             if (RESCALE) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v] *= scl[v];

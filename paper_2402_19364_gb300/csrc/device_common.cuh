@@ -165,10 +165,40 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 #ifndef ARROW_SEG_MIN_BLOCKS
 #define ARROW_SEG_MIN_BLOCKS 4
 #endif
+// 1: a segment's last 1..7 entries of a team are gathered in one round; 0: one at a time.
+#ifndef ARROW_SEG_EXACT_TAIL
+#define ARROW_SEG_EXACT_TAIL 1
+#endif
+// R entries j, j + S, ..., j + (R-1) S of a split-row segment (columns and values from
+// global memory), their gathers issued together, accumulated in that order.
+template <int R, typename TX, typename TV, int S>
+__device__ __forceinline__ void segment_tail(const int32_t* __restrict__ col, const TV* __restrict__ val,
+                                             const TX* __restrict__ X, int64_t ldx, int j, float* acc) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    int32_t c[R];
+    float w[R];
+    uint4 x[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) c[u] = ld_stream_i32(col + j + u * S);
+#pragma unroll
+    for (int u = 0; u < R; ++u) w[u] = val_to_float(ld_stream_val<TV>(val + j + u * S));
+#pragma unroll
+    for (int u = 0; u < R; ++u) x[u] = ld_x(X + int64_t(c[u]) * ldx);
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        float f[V];
+        P::to_float(x[u], f);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = fmaf(w[u], f[v], acc[v]);
+    }
+}
+
 template <typename TX, typename TV, int T, int U = 8>
 __device__ __forceinline__ void segment_partial(const int32_t* __restrict__ col, const TV* __restrict__ val,
                                                       const TX* __restrict__ X, int64_t ldx, int s, int e, int lane,
                                                       float* acc) {
+    static_assert(U <= 8, "the tail round below handles up to 7 remaining entries");
     using P = Pack<TX>;
     constexpr int V = P::V;
     constexpr int TPW = 32 / T;
@@ -194,14 +224,22 @@ __device__ __forceinline__ void segment_partial(const int32_t* __restrict__ col,
             for (int v = 0; v < V; ++v) acc[v] = fmaf(w[u], f[v], acc[v]);
         }
     }
-    for (; j < e; j += TPW) {
-        const int32_t c = ld_stream_i32(col + j);
-        const float w = val_to_float(ld_stream_val<TV>(val + j));
-        float f[V];
-        P::to_float(ld_x(X + int64_t(c) * ldx), f);
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = fmaf(w, f[v], acc[v]);
+#if ARROW_SEG_EXACT_TAIL
+    // the team's last 0..U-1 entries j, j + TPW, ...: one round of exactly that many gathers
+    // (one at a time, each would wait a full latency); same order of accumulation
+    switch (j < e ? (e - j + TPW - 1) / TPW : 0) {
+        case 7: segment_tail<7, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
+        case 6: segment_tail<6, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
+        case 5: segment_tail<5, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
+        case 4: segment_tail<4, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
+        case 3: segment_tail<3, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
+        case 2: segment_tail<2, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
+        case 1: segment_tail<1, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
+        default: break;
     }
+#else
+    for (; j < e; j += TPW) segment_tail<1, TX, TV, TPW>(col, val, X, ldx, j, acc);
+#endif
 }
 
 // One gather round of a row staged in shared memory: the R entries base..base+R-1 (column
