@@ -579,7 +579,8 @@ def time_calls(arrow, M, Xd, Yd, iters, rescale, steps, warmup, pg, stream, flus
     for _ in range(warmup):
         M.spmm(Xd, iters, rescale=rescale, out=Yd)
     torch.cuda.synchronize()
-    for kind in (arrow.ARROW_K_ROWS, arrow.ARROW_K_SEGMENTS, arrow.ARROW_K_NORM, arrow.ARROW_K_PERMUTE):
+    for kind in (arrow.ARROW_K_ROWS, arrow.ARROW_K_SEGMENTS, arrow.ARROW_K_NORM, arrow.ARROW_K_PERMUTE,
+                 arrow.ARROW_K_FUSED):
         M.profile_get(kind)
     barrier(pg)
     torch.cuda.synchronize()
@@ -601,13 +602,16 @@ def time_calls(arrow, M, Xd, Yd, iters, rescale, steps, warmup, pg, stream, flus
     ms_total = max_over_ranks(pg, ms_total)
     km, launches = {}, 0
     for name, kind in (("rows", arrow.ARROW_K_ROWS), ("segments", arrow.ARROW_K_SEGMENTS),
-                       ("norm", arrow.ARROW_K_NORM), ("permute", arrow.ARROW_K_PERMUTE)):
+                       ("norm", arrow.ARROW_K_NORM), ("permute", arrow.ARROW_K_PERMUTE),
+                       ("fused", arrow.ARROW_K_FUSED)):
         ms, cnt = M.profile_get(kind)
         km[name] = ms
         km[name + "_launches"] = cnt
         launches += cnt
-    return {"ms_total": ms_total, "launches": launches, "kernel_ms": {c: km[c] for c in ("rows", "segments", "norm", "permute")},
+    return {"ms_total": ms_total, "launches": launches,
+            "kernel_ms": {c: km[c] for c in ("rows", "segments", "norm", "permute", "fused")},
             "rows_launches": km["rows_launches"], "segments_launches": km["segments_launches"],
+            "fused_launches": km["fused_launches"], "iters_per_call": iters,
             "step_ms": {"mean": sum(step_ms) / len(step_ms), "min": min(step_ms), "max": max(step_ms)}}
 
 
@@ -618,7 +622,14 @@ def roofline_record(M, k, dt_name, tm, spec, peak, peak_kind):
     iteration from the committed ncu summary, when it was taken on this kernel source and
     this workload (spec None: not looked up)."""
     ab = M.algorithmic_bytes_per_iter(k, dt_name)
-    per_launch_s = (tm["kernel_ms"]["rows"] + tm["kernel_ms"]["segments"]) / max(1, tm["rows_launches"]) / 1e3
+    if tm["fused_launches"]:
+        # the one-launch path: the whole call in one kernel; per iteration = its time / iterations
+        per_launch_s = tm["kernel_ms"]["fused"] / (tm["fused_launches"] * tm["iters_per_call"]) / 1e3
+        kernel = "arrow_fused_small_kernel (whole call, per iteration)"
+    else:
+        per_launch_s = (tm["kernel_ms"]["rows"] + tm["kernel_ms"]["segments"]) / max(1, tm["rows_launches"]) / 1e3
+        kernel = "arrow_rows_kernel" + (" + arrow_segments_kernel + arrow_combine_kernel"
+                                        if tm["segments_launches"] else "")
     achieved = ab["total"] / per_launch_s / 1e9
     traffic = None
     tr = kernel_traffic(workload_key(spec)) if spec is not None else None
@@ -628,9 +639,7 @@ def roofline_record(M, k, dt_name, tm, spec, peak, peak_kind):
         except (KeyError, ValueError):
             traffic = None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_kind": peak_kind,
-            "kernel": "arrow_rows_kernel" + (" + arrow_segments_kernel + arrow_combine_kernel"
-                                             if tm["segments_launches"] else ""),
+            "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
             "algorithmic_bytes_per_launch": ab["total"], "launch_ms": per_launch_s * 1e3,
             "frac_of_nominal_8000": achieved / 8000.0}
 

@@ -95,13 +95,19 @@ int arrow_opts_default(arrow_opts* o);
  * fold_permute_in = 1, which makes the first iteration gather straight from the caller's X
  * through a second copy of the column indices in vertex ids (4 bytes per entry of device
  * memory, set up when the setting is applied) instead of permuting X into pi_0 order first.
- * Defaults: 256, 2048, 4, 70, 0. */
+ * fused_small = 1 runs a whole arrow_spmm call as one cooperative launch (permute-in, every
+ * iteration's phases separated by grid-wide barriers with a 2 s limit, permute-out) when the
+ * problem is small (n <= 2^20, nnz <= 2^23) and k / (16 / sizeof(x_dtype)) <= 32, where kernel
+ * start-up would dominate; identical results without ARROW_RESCALE, within rounding with it
+ * (the FP64 column sums are grouped differently).  Larger problems ignore it.
+ * Defaults: 256, 2048, 4, 70, 0, 0. */
 typedef struct {
     int32_t tile_rows;
     int32_t tile_nnz;
     int32_t ctas_per_sm;
     int32_t carveout;
     int32_t fold_permute_in;
+    int32_t fused_small;
 } arrow_tuning;
 
 
@@ -113,12 +119,13 @@ int arrow_get_tuning(arrow_handle h, arrow_tuning* t);
 /* Re-tile the handle (host, O(n)) and, if uploaded, replace its device tile tables; waits for
  * the device first.  Errors: ARROW_EINVAL (out of range: 32 <= tile_rows <= 2048,
  * 1024 <= tile_nnz <= 16384, 1 <= ctas_per_sm <= 4, 0 <= carveout <= 100,
- * fold_permute_in 0 or 1), ARROW_ENOMEM, ARROW_ECUDA. */
+ * fold_permute_in and fused_small 0 or 1), ARROW_ENOMEM, ARROW_ECUDA. */
 int arrow_set_tuning(arrow_handle h, const arrow_tuning* t);
 
 /* arrow_autotune -- time a fixed set of tunings (tile shapes 128/1024, 256/2048, 384/3072,
- * 512/4096 rows/entries x 2..4 CTAs per SM that fit, carveout fitted to them; then the best of
- * those with fold_permute_in switched) with arrow_spmm on the caller's X, Y (as arrow_spmm) for
+ * 512/4096 rows/entries x 2..4 CTAs per SM that fit, carveout fitted to them; then, for a small
+ * problem, the one-launch path (fused_small); then the best multi-launch shape with
+ * fold_permute_in switched) with arrow_spmm on the caller's X, Y (as arrow_spmm) for
  * `iters` iterations each (one warm-up call, two timed), keep the fastest on the handle, and
  * return it with its milliseconds per call.  Synchronises `stream`.
  * Errors: as arrow_spmm and arrow_set_tuning. */
@@ -398,6 +405,7 @@ int arrow_get_stats(arrow_handle h, arrow_stats* s);
 #define ARROW_K_SEGMENTS 1   /* split-row segment kernel (first stage of the head-row reduction) */
 #define ARROW_K_NORM     2   /* FP64 column-norm finalize                                    */
 #define ARROW_K_PERMUTE  3   /* permute-in / permute-out gathers                             */
+#define ARROW_K_FUSED    4   /* the one-launch path (whole call in one cooperative kernel)   */
 
 /* arrow_profile_get -- device time of the launches recorded by arrow_spmm calls made with
  * ARROW_PROFILE since the last arrow_profile_get, for one kernel class: total milliseconds

@@ -12,7 +12,8 @@ import ctypes
 import numpy as np
 
 from . import _native
-from ._native import (ARROW_BF16, ARROW_F16, ARROW_F32, ARROW_GRAPH, ARROW_HOST_ONLY, ARROW_K_NORM, ARROW_K_PERMUTE,
+from ._native import (ARROW_BF16, ARROW_F16, ARROW_F32, ARROW_GRAPH, ARROW_HOST_ONLY, ARROW_K_FUSED, ARROW_K_NORM,
+                      ARROW_K_PERMUTE,
                       ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_PRED_BAND, ARROW_PRED_BLOCK, ARROW_PROFILE,
                       ARROW_RELU, ARROW_RESCALE, ARROW_ROWNORM, ArrowError)
 
@@ -253,10 +254,14 @@ class ArrowMatrix:
         return {f: getattr(t, f) for f, _ in t._fields_}
 
     def set_tuning(self, tile_rows: int, tile_nnz: int, ctas_per_sm: int, carveout: int,
-                   fold_permute_in: int | None = None) -> None:
+                   fold_permute_in: int | None = None, fused_small: int | None = None) -> None:
+        cur = self.tuning
         if fold_permute_in is None:
-            fold_permute_in = self.tuning["fold_permute_in"]
-        t = _native.ArrowTuning(int(tile_rows), int(tile_nnz), int(ctas_per_sm), int(carveout), int(fold_permute_in))
+            fold_permute_in = cur["fold_permute_in"]
+        if fused_small is None:
+            fused_small = cur["fused_small"]
+        t = _native.ArrowTuning(int(tile_rows), int(tile_nnz), int(ctas_per_sm), int(carveout), int(fold_permute_in),
+                                int(fused_small))
         _native.check(_native.lib().arrow_set_tuning(self._h, ctypes.byref(t)))
 
     def autotune(self, X, iters: int, *, rescale: bool = False, out=None, stream=None):

@@ -24,7 +24,7 @@ ARROW_PROFILE = 0x2
 ARROW_GRAPH = 0x4
 ARROW_RELU = 0x8
 ARROW_ROWNORM = 0x10
-ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_K_NORM, ARROW_K_PERMUTE = 0, 1, 2, 3
+ARROW_K_ROWS, ARROW_K_SEGMENTS, ARROW_K_NORM, ARROW_K_PERMUTE, ARROW_K_FUSED = 0, 1, 2, 3, 4
 
 
 class ArrowError(RuntimeError):
@@ -66,7 +66,8 @@ class ArrowProgram(ctypes.Structure):
 
 class ArrowTuning(ctypes.Structure):
     _fields_ = [("tile_rows", ctypes.c_int32), ("tile_nnz", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("carveout", ctypes.c_int32), ("fold_permute_in", ctypes.c_int32)]
+                ("carveout", ctypes.c_int32), ("fold_permute_in", ctypes.c_int32),
+                ("fused_small", ctypes.c_int32)]
 
 
 class ArrowServerOpts(ctypes.Structure):

@@ -306,7 +306,7 @@ int arrow_batch_autotune(arrow_batch B, const void* const* X, void* const* Y, co
             const int per = batch_smem_bytes(L) + 1024;
             if (ctas * per > 227 * 1024) break;             // would not be resident together
             const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);
-            arrow_tuning cand{sh[0], sh[1], ctas, pct, B->hs[0]->tune.fold_permute_in};
+            arrow_tuning cand{sh[0], sh[1], ctas, pct, B->hs[0]->tune.fold_permute_in, B->hs[0]->tune.fused_small};
             if ((rc = apply(cand))) break;
             if ((rc = arrow_batch_spmm(B, X, Y, k, iters, x_dtype, ARROW_GRAPH, stream))) break;
             cudaEventRecord(e0, s);

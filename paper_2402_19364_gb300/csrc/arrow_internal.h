@@ -102,7 +102,7 @@ struct arrow_handle_s {
     std::vector<int32_t> long_rows, long_segptr, seg_begin, seg_end;
     std::vector<int32_t> tile_row, tile_ent;
     int32_t long_row = arrow::kDefaultLongRow;
-    arrow_tuning tune{arrow::kTileRows, arrow::kTileNnz, 4, 70, 0};
+    arrow_tuning tune{arrow::kTileRows, arrow::kTileNnz, 4, 70, 0, 0};
     double decompose_seconds = 0.0;
     bool uploaded = false;
     // bumped whenever the device arrays or the tile table change (upload, re-tiling):

@@ -449,6 +449,226 @@ __global__ void __launch_bounds__(256) arrow_gather_rows_kernel(const TX* __rest
     }
 }
 
+// ------------------------------------------------------------------------------------
+// one-launch path for small problems
+// ------------------------------------------------------------------------------------
+// Grid-wide barrier of a cooperative launch (every CTA resident): sense by generation count.
+// Thread 0 of each CTA arrives; the last one resets the counter and advances the generation;
+// the others wait for the generation to move, at most limit_ns.  Returns false (in every
+// thread of the CTA) when the wait ran out.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned G, uint64_t limit_ns) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        volatile unsigned* vg = gen;
+        const unsigned g0 = *vg;
+        __threadfence();
+        if (atomicAdd(count, 1u) == G - 1) {
+            *reinterpret_cast<volatile unsigned*>(count) = 0;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (*vg == g0) {
+                if (global_ns() - t0 > limit_ns) { ok = 0; break; }
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+struct FusedArgs {
+    const int32_t* rowptr;
+    const int32_t* col;
+    const void* val;
+    const int32_t* lcol;
+    const void* lval;
+    const int32_t* seg_begin;
+    const int32_t* seg_end;
+    const int32_t* long_rows;
+    const int32_t* long_segptr;
+    const int32_t* perm0;
+    const int32_t* iperm0;
+    int64_t n, n_seg, n_long;
+    const void* X;          // caller's X (vertex order)
+    void* Y;                // caller's Y (vertex order)
+    void* xa;
+    void* xb;
+    float* partials;        // [n_seg][k]
+    double* np;             // [2][gridDim.x][k] FP64 column sums, by iteration parity
+    int64_t k;
+    int32_t iters, sigma;
+    unsigned* bar;          // [0] arrival count, [1] generation
+    int32_t* status;
+};
+
+// The whole arrow_spmm call in one cooperative launch, for problems small enough that kernel
+// start-up dominates: the permute-in, then per iteration the split-row segments and the rows
+// (one phase), the combine of the split rows, and the FP64 column sums (every CTA sums the
+// per-CTA partials itself, in the same order), then the permute-out.  Each row and segment is
+// computed with the same code and order as the multi-launch path (identical bits without the
+// rescale; with it the column sums are grouped by this launch's CTAs).  Needs k / V <= 32 (one
+// chunk).  A barrier that runs out sets the status word and the kernel returns.
+template <typename TX, typename TV, int T, bool RESCALE>
+__global__ void __launch_bounds__(256) arrow_fused_small_kernel(FusedArgs a) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    constexpr int TEAMS = 256 / T;
+    const int lane = threadIdx.x & 31;
+    const int tl = threadIdx.x & (T - 1);
+    const int team = threadIdx.x / T;
+    const int col0 = tl * V;
+    const int64_t G = gridDim.x;
+    const int64_t gteam = int64_t(blockIdx.x) * TEAMS + team, nteams = G * TEAMS;
+    const int64_t gwarp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5, nwarps = (G * blockDim.x) >> 5;
+    const int64_t k = a.k;
+    __shared__ double wsum[TEAMS * T * V];   // per-team FP64 column sums (RESCALE)
+    __shared__ float scl_s[T * V];           // this iteration's column factors
+    const TV* val = static_cast<const TV*>(a.val);
+    const TV* lval = static_cast<const TV*>(a.lval);
+
+    // permute-in: xa[p] = X[pi_0^{-1}(p)]
+    {
+        const TX* src = static_cast<const TX*>(a.X);
+        TX* dst = static_cast<TX*>(a.xa);
+        for (int64_t p = gteam; p < a.n; p += nteams)
+            *reinterpret_cast<uint4*>(dst + p * k + col0) = ld_x(src + int64_t(__ldg(a.iperm0 + p)) * k + col0);
+    }
+    for (int c = threadIdx.x; c < T * V; c += blockDim.x) scl_s[c] = 1.0f;
+    if (!grid_barrier(a.bar, a.bar + 1, unsigned(G), kWaitLimitNs)) {
+        if (threadIdx.x == 0) atomicExch(a.status, kStatusTimeout);
+        return;
+    }
+    TX* cur = static_cast<TX*>(a.xa);
+    TX* nxt = static_cast<TX*>(a.xb);
+    for (int t = 1; t <= a.iters; ++t) {
+        float scl[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) scl[v] = scl_s[col0 + v];
+        float sq[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) sq[v] = 0.f;
+        // split-row segments (first stage of the head-row reduction)
+        for (int64_t g = gwarp; g < a.n_seg; g += nwarps) {
+            const int32_t s = __ldg(a.seg_begin + g), e = __ldg(a.seg_end + g);
+            float acc[V];
+            segment_partial<TX, TV, T>(a.lcol, lval, cur + col0, k, s, e, lane, acc);
+#pragma unroll
+            for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+            if (lane < T) {
+                float4* q = reinterpret_cast<float4*>(a.partials + g * k + col0);
+#pragma unroll
+                for (int u = 0; u < V / 4; ++u) q[u] = make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
+            }
+        }
+        // rows: the fused arrow rows of every level, in entry order
+        for (int64_t p = gteam; p < a.n; p += nteams) {
+            const int s = __ldg(a.rowptr + p), e = __ldg(a.rowptr + p + 1);
+            float acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = 0.f;
+            gather_row<TX, TV>(a.col, val, s, e, cur + col0, k, acc);
+            if (RESCALE) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+            }
+            if (a.sigma) apply_sigma<T, V>(acc, a.sigma, lane);
+            const uint4 out = P::from_float(acc);
+            *reinterpret_cast<uint4*>(nxt + p * k + col0) = out;
+            if (RESCALE && (a.n_long == 0 || s < e)) {   // split rows are summed after the combine
+                float yr[V];
+                P::to_float(out, yr);
+#pragma unroll
+                for (int v = 0; v < V; ++v) sq[v] = fmaf(yr[v], yr[v], sq[v]);
+            }
+        }
+        if (a.n_long) {
+            if (!grid_barrier(a.bar, a.bar + 1, unsigned(G), kWaitLimitNs)) {
+                if (threadIdx.x == 0) atomicExch(a.status, kStatusTimeout);
+                return;
+            }
+            // second stage of the head-row reduction: segment partials in segment order
+            for (int64_t li = gteam; li < a.n_long; li += nteams) {
+                float acc[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = 0.f;
+                const int g0 = __ldg(a.long_segptr + li), g1 = __ldg(a.long_segptr + li + 1);
+                for (int g = g0; g < g1; ++g) {
+                    const float4* q = reinterpret_cast<const float4*>(a.partials + int64_t(g) * k + col0);
+#pragma unroll
+                    for (int u = 0; u < V / 4; ++u) {
+                        const float4 f = q[u];
+                        acc[4 * u + 0] += f.x; acc[4 * u + 1] += f.y; acc[4 * u + 2] += f.z; acc[4 * u + 3] += f.w;
+                    }
+                }
+                if (RESCALE) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] *= scl[v];
+                }
+                if (a.sigma) apply_sigma<T, V>(acc, a.sigma, lane);
+                const uint4 out = P::from_float(acc);
+                *reinterpret_cast<uint4*>(nxt + int64_t(__ldg(a.long_rows + li)) * k + col0) = out;
+                if (RESCALE) {
+                    float yr[V];
+                    P::to_float(out, yr);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) sq[v] = fmaf(yr[v], yr[v], sq[v]);
+                }
+            }
+        }
+        if (RESCALE) {
+            // this CTA's FP64 column sums: lanes' FP32 squares per team, teams in order
+#pragma unroll
+            for (int v = 0; v < V; ++v) wsum[team * (T * V) + col0 + v] = double(sq[v]);
+            __syncthreads();
+            double* npo = a.np + int64_t(t & 1) * G * k;
+            for (int c = threadIdx.x; c < T * V; c += blockDim.x) {
+                double acc = 0.0;
+                for (int t2 = 0; t2 < TEAMS; ++t2) acc += wsum[t2 * (T * V) + c];
+                npo[int64_t(blockIdx.x) * k + c] = acc;
+            }
+        }
+        if (!grid_barrier(a.bar, a.bar + 1, unsigned(G), kWaitLimitNs)) {
+            if (threadIdx.x == 0) atomicExch(a.status, kStatusTimeout);
+            return;
+        }
+        if (RESCALE) {
+            // every CTA sums the partials of all CTAs in the same order: the same factors
+            const double* npi = a.np + int64_t(t & 1) * G * k;
+            for (int c = threadIdx.x; c < T * V; c += blockDim.x) {
+                double acc = 0.0;
+                for (int64_t b = 0; b < G; ++b) acc += npi[b * k + c];
+                scl_s[c] = acc > 0.0 ? float(1.0 / sqrt(acc)) : 1.0f;
+            }
+            __syncthreads();
+        }
+        TX* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    // permute-out: Y[v] = cur[pi_0(v)] (* the last column factors)
+    {
+        float scl[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) scl[v] = scl_s[col0 + v];
+        TX* dst = static_cast<TX*>(a.Y);
+        for (int64_t v = gteam; v < a.n; v += nteams) {
+            uint4 o = ld_x(cur + int64_t(__ldg(a.perm0 + v)) * k + col0);
+            if (RESCALE) {
+                float f[V];
+                P::to_float(o, f);
+#pragma unroll
+                for (int u = 0; u < V; ++u) f[u] *= scl[u];
+                o = P::from_float(f);
+            }
+            *reinterpret_cast<uint4*>(dst + v * k + col0) = o;
+        }
+    }
+}
+
 template <typename TV>
 __global__ void arrow_convert_values_kernel(const double* __restrict__ src, TV* __restrict__ dst, int64_t n);
 template <>
@@ -662,6 +882,7 @@ static int upload_to_current(arrow_handle_s* h) {
 // ---- launch plumbing -----------------------------------------------------------------
 struct Plan {
     int V, T, chunks, kc;
+    int fused_grid;  // CTAs of the one-launch path (arrow_fused_small_kernel), 0 = multi-launch path
     int rows_grid;   // CTAs of the rows kernel (= its FP64 norm partial slots)
     int comb_grid;   // CTAs of the combine kernel (= its partial slots after the rows kernel's)
     size_t x_bytes, part_bytes, np_bytes, sc_bytes, total;
@@ -701,6 +922,14 @@ int require_device(int device, const char* what) {
     return ARROW_OK;
 }
 
+// Problems the one-launch path takes: up to 1M rows and 8M entries (beyond that the
+// multi-launch path's start-up is small against the work).
+static bool fused_eligible(const arrow_handle_s* h, int64_t k, int x_dtype) {
+    (void)k;
+    (void)x_dtype;
+    return h->n <= (int64_t(1) << 20) && h->nnz <= (int64_t(8) << 20);
+}
+
 static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags, Plan& p) {
     p.V = int(16 / dtype_size(x_dtype));
     if (k % p.V) { set_error("arrow_spmm: k * sizeof(dtype) must be a multiple of 16 bytes"); return ARROW_EINVAL; }
@@ -729,7 +958,15 @@ static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags,
     const size_t sx = dtype_size(x_dtype);
     p.x_bytes = align256(size_t(h->n) * size_t(k) * sx);
     p.part_bytes = align256(std::max<size_t>(1, h->seg_begin.size()) * size_t(p.kc) * 4);
-    p.np_bytes = (flags & ARROW_RESCALE) ? align256(size_t(p.rows_grid + p.comb_grid) * size_t(k) * 8) : 0;
+    // the one-launch path: asked for by the tuning, for one-chunk k and small problems (where
+    // kernel start-up dominates), one CTA per 4 rows per team, at most one per SM (all resident)
+    p.fused_grid = 0;
+    if (h->tune.fused_small && p.chunks == 1 && fused_eligible(h, k, x_dtype)) {
+        const int64_t per_cta = int64_t(256 / p.T) * 4;
+        p.fused_grid = int(std::max<int64_t>(1, std::min<int64_t>((h->n + per_cta - 1) / per_cta, sm)));
+    }
+    const size_t np_slots = std::max<size_t>(size_t(p.rows_grid + p.comb_grid), size_t(2 * p.fused_grid));
+    p.np_bytes = (flags & ARROW_RESCALE) ? align256(np_slots * size_t(k) * 8) : 0;
     p.sc_bytes = (flags & ARROW_RESCALE) ? align256(2 * size_t(k) * 8) : 0;
     p.total = 2 * p.x_bytes + p.part_bytes + p.np_bytes + p.sc_bytes;
     return ARROW_OK;
@@ -817,6 +1054,50 @@ static void run_steps(const arrow_handle_s* h, const Plan& p, const TX* x_first,
     *final_buf = const_cast<TX*>(cur);
 }
 
+template <typename TX, typename TV, int T>
+static cudaError_t launch_fused_t(const Plan& p, FusedArgs& fa, bool rescale, cudaStream_t s) {
+    void* args[] = {&fa};
+    const void* fn = rescale ? reinterpret_cast<const void*>(arrow_fused_small_kernel<TX, TV, T, true>)
+                             : reinterpret_cast<const void*>(arrow_fused_small_kernel<TX, TV, T, false>);
+    return cudaLaunchCooperativeKernel(fn, dim3(p.fused_grid), dim3(256), args, 0, s);
+}
+
+template <typename TX, typename TV>
+static cudaError_t launch_fused_v(const Plan& p, FusedArgs& fa, bool rescale, cudaStream_t s) {
+    switch (p.T) {
+        case 1: return launch_fused_t<TX, TV, 1>(p, fa, rescale, s);
+        case 2: return launch_fused_t<TX, TV, 2>(p, fa, rescale, s);
+        case 4: return launch_fused_t<TX, TV, 4>(p, fa, rescale, s);
+        case 8: return launch_fused_t<TX, TV, 8>(p, fa, rescale, s);
+        case 16: return launch_fused_t<TX, TV, 16>(p, fa, rescale, s);
+        default: return launch_fused_t<TX, TV, 32>(p, fa, rescale, s);
+    }
+}
+
+// The whole call as one cooperative launch (arrow_fused_small_kernel); the barrier counter
+// is cleared on the stream first.
+template <typename TX>
+static int launch_fused(const arrow_handle_s* h, const Plan& p, const void* X, int64_t k, int iters, void* Y, int flags,
+                        char* ws, float* part, double* np, cudaStream_t s, Prof& pf) {
+    const DeviceData& d = h->dev;
+    FusedArgs fa{d.rowptr, d.col, d.val, d.lcol, d.lval, d.seg_begin, d.seg_end, d.long_rows, d.long_segptr, d.perm0,
+                 d.iperm0, h->n, int64_t(h->seg_begin.size()), int64_t(h->long_rows.size()), X, Y, ws,
+                 ws + p.x_bytes, part, np, k, iters, sigma_of(flags), reinterpret_cast<unsigned*>(d.status + 2),
+                 d.status};
+    ACK(cudaMemsetAsync(d.status + 2, 0, sizeof(int32_t), s));
+    cudaEvent_t e0 = pf.begin();
+    cudaError_t e;
+    const bool rescale = flags & ARROW_RESCALE;
+    switch (h->opts.value_dtype) {
+        case ARROW_F32: e = launch_fused_v<TX, float>(p, fa, rescale, s); break;
+        case ARROW_BF16: e = launch_fused_v<TX, __nv_bfloat16>(p, fa, rescale, s); break;
+        default: e = launch_fused_v<TX, __half>(p, fa, rescale, s); break;
+    }
+    pf.end(ARROW_K_FUSED, e0);
+    if (e != cudaSuccess) return cuda_fail(e, "arrow_spmm: one-launch path");
+    return ARROW_OK;
+}
+
 template <typename TX>
 static int spmm_typed(const arrow_handle_s* h, const Plan& p, const void* X, int64_t k, int iters, void* Y, int flags,
                       char* ws, cudaStream_t s, Prof& pf) {
@@ -827,6 +1108,7 @@ static int spmm_typed(const arrow_handle_s* h, const Plan& p, const void* X, int
     double* np = reinterpret_cast<double*>(ws + 2 * p.x_bytes + p.part_bytes);
     double* sc = reinterpret_cast<double*>(ws + 2 * p.x_bytes + p.part_bytes + p.np_bytes);
     const int64_t n = h->n;
+    if (p.fused_grid > 0) return launch_fused<TX>(h, p, X, k, iters, Y, flags, ws, part, np, s, pf);
     const int64_t vecs = n * (k / p.V);
     const int ggrid = int(std::max<int64_t>(1, std::min<int64_t>((vecs + 2047) / 2048, int64_t(d.sm_count) * 8)));
     // permute-in, unless the first iteration reads the caller's X through vertex-id indices
@@ -1201,7 +1483,7 @@ int arrow_set_tuning(arrow_handle h, const arrow_tuning* t) {
     if (!h || !t) { set_error("arrow_set_tuning: NULL argument"); return ARROW_EINVAL; }
     if (t->tile_rows < 32 || t->tile_rows > kMaxTileRows || t->tile_nnz < kMinTileNnz || t->tile_nnz > kMaxTileNnz ||
         t->ctas_per_sm < 1 || t->ctas_per_sm > ARROW_ROWS_MIN_BLOCKS || t->carveout < 0 || t->carveout > 100 ||
-        t->fold_permute_in < 0 || t->fold_permute_in > 1) {
+        t->fold_permute_in < 0 || t->fold_permute_in > 1 || t->fused_small < 0 || t->fused_small > 1) {
         set_error("arrow_set_tuning: value out of range");
         return ARROW_EINVAL;
     }
@@ -1250,7 +1532,7 @@ int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t it
             const int per = rows_smem_bytes(L, (flags & ARROW_RESCALE) ? 256 * int(16 / dtype_size(x_dtype)) : 0) + 1024;
             if (ctas * per > 227 * 1024) break;
             const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);
-            arrow_tuning cand{sh[0], sh[1], ctas, pct, h->tune.fold_permute_in};
+            arrow_tuning cand{sh[0], sh[1], ctas, pct, h->tune.fold_permute_in, 0};
             if ((rc = arrow_set_tuning(h, &cand))) break;
             if ((rc = arrow_spmm(h, X, k, iters, Y, x_dtype, flags, stream))) break;
             cudaEventRecord(e0, s);
@@ -1264,7 +1546,22 @@ int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t it
         }
         if (rc) break;
     }
-    if (rc == ARROW_OK && h->n > 0) {
+    // the one-launch path, where the problem is small enough for it
+    if (rc == ARROW_OK && h->n > 0 && fused_eligible(h, k, x_dtype) && int64_t(16 / dtype_size(x_dtype)) * 32 >= k) {
+        arrow_tuning cand = bt;
+        cand.fused_small = 1;
+        if ((rc = arrow_set_tuning(h, &cand)) == ARROW_OK && (rc = arrow_spmm(h, X, k, iters, Y, x_dtype, flags, stream)) == ARROW_OK) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 2 && rc == ARROW_OK; ++r) rc = arrow_spmm(h, X, k, iters, Y, x_dtype, flags, stream);
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) rc = cuda_fail(e, "arrow_autotune");
+            else if (ms / 2 < bms) { bms = ms / 2; bt = cand; }
+        }
+    }
+    if (rc == ARROW_OK && h->n > 0 && !bt.fused_small) {
         // the best shape with the permute-in folded into the first iteration, or not
         arrow_tuning cand = bt;
         cand.fold_permute_in = bt.fold_permute_in ? 0 : 1;

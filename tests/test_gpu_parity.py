@@ -203,6 +203,52 @@ def test_folded_permute_in_keeps_the_bits(arrow, dt, k, rescale):
     assert (err_inf(Yn, R) <= 6e-5) if dt == "f32" else (err_2(Yn, R) <= 2e-2)
 
 
+@pytest.mark.parametrize("case", ["grid2d_f32", "rmat_split_bf16", "rgg_f16_k8", "grid_sigma_f32"])
+def test_one_launch_path(arrow, case):
+    """fused_small = 1: the whole call as one cooperative launch.  Without the rescale it gives
+    the multi-launch path's bits (same row, segment and combine arithmetic); with it, the FP64
+    column sums are grouped by its CTAs, so it agrees within the FP32 bar; both match the oracle."""
+    kw, sig = {}, {}
+    if case == "grid2d_f32":
+        A, b, k, dt, it = w.grid2d_64(seed=1), 64, 16, "f32", 10
+    elif case == "rmat_split_bf16":
+        A, b, k, dt, it = w.rmat_gcn(12, 16, seed=5), 64, 128, "bf16", 5
+        kw = {"long_row": 16, "segment": 48}
+    elif case == "rgg_f16_k8":
+        A = w.rgg(6000, seed=7)
+        b, k, dt, it = int(np.ceil(np.sqrt(A.n))), 8, "f16", 10
+    else:
+        A, b, k, dt, it = w.grid_stencil((45, 38), seed=9), 45, 32, "f32", 6
+        sig = {"relu": True, "rownorm": True}
+    X = w.features(A.n, k, seed=11)
+    M = arrow.ArrowMatrix(A, b, value_dtype=dt, **kw)
+    if kw:
+        assert M.stats()["segments"] > 0
+    Xd = torch.from_numpy(X).to("cuda", TORCH_DT[dt])
+    t = M.tuning
+    for rescale in (False, True):
+        M.set_tuning(t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"], 0, 0)
+        ref = M.spmm(Xd, it, rescale=rescale, **sig)
+        M.set_tuning(t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"], 0, 1)
+        Y = M.spmm(Xd, it, rescale=rescale, **sig, profile=True)
+        torch.cuda.synchronize()
+        assert M.profile_get(arrow.ARROW_K_FUSED)[1] == 1          # the one-launch path ran
+        assert M.profile_get(arrow.ARROW_K_ROWS)[1] == 0
+        assert M.status() == 0
+        Yn = Y.float().cpu().numpy().astype(np.float64)
+        R = S.iterate(A, X, it, rescale=rescale, rectify=bool(sig), rownorm=bool(sig))
+        if not rescale:
+            assert torch.equal(Y, ref)
+        if dt == "f32":
+            assert err_inf(Yn, R) <= 1e-5 * it
+            assert err_inf(Yn, ref.cpu().numpy().astype(np.float64)) <= 2e-5 * it
+        else:
+            assert err_2(Yn, R) <= 2e-2
+        Xa = Xd.clone()
+        M.spmm(Xa, it, rescale=rescale, out=Xa, **sig)               # X and Y may alias
+        assert torch.equal(Xa, Y)
+
+
 def test_iters_zero_alias_and_determinism(arrow):
     A = w.grid_stencil((37, 29), seed=9)            # ragged: n = 1073 is not a multiple of b
     X = w.features(A.n, 32, seed=10)
