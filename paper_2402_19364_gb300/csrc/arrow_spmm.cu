@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(256) arrow_fused_small_kernel(FusedArgs a) {
         const TX* src = static_cast<const TX*>(a.X);
         TX* dst = static_cast<TX*>(a.xa);
         for (int64_t p = gteam; p < a.n; p += nteams)
-            *reinterpret_cast<uint4*>(dst + p * k + col0) = ld_x(src + int64_t(__ldg(a.iperm0 + p)) * k + col0);
+            *reinterpret_cast<uint4*>(dst + p * k + col0) = ld_x_cg(src + int64_t(__ldg(a.iperm0 + p)) * k + col0);
     }
     for (int c = threadIdx.x; c < T * V; c += blockDim.x) scl_s[c] = 1.0f;
     if (!grid_barrier(a.bar, a.bar + 1, unsigned(G), kWaitLimitNs)) {
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(256) arrow_fused_small_kernel(FusedArgs a) {
         for (int64_t g = gwarp; g < a.n_seg; g += nwarps) {
             const int32_t s = __ldg(a.seg_begin + g), e = __ldg(a.seg_end + g);
             float acc[V];
-            segment_partial<TX, TV, T>(a.lcol, lval, cur + col0, k, s, e, lane, acc);
+            segment_partial<TX, TV, T, 8, true>(a.lcol, lval, cur + col0, k, s, e, lane, acc);
 #pragma unroll
             for (int off = T; off < 32; off <<= 1)
 #pragma unroll
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(256) arrow_fused_small_kernel(FusedArgs a) {
             float acc[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.f;
-            gather_row<TX, TV>(a.col, val, s, e, cur + col0, k, acc);
+            gather_row<TX, TV, true>(a.col, val, s, e, cur + col0, k, acc);
             if (RESCALE) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v] *= scl[v];
@@ -597,10 +597,12 @@ __global__ void __launch_bounds__(256) arrow_fused_small_kernel(FusedArgs a) {
                 for (int v = 0; v < V; ++v) acc[v] = 0.f;
                 const int g0 = __ldg(a.long_segptr + li), g1 = __ldg(a.long_segptr + li + 1);
                 for (int g = g0; g < g1; ++g) {
-                    const float4* q = reinterpret_cast<const float4*>(a.partials + int64_t(g) * k + col0);
+                    const float* q = a.partials + int64_t(g) * k + col0;
 #pragma unroll
                     for (int u = 0; u < V / 4; ++u) {
-                        const float4 f = q[u];
+                        const uint4 r = ld_x_cg(q + 4 * u);
+                        const float4 f = make_float4(__uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z),
+                                                     __uint_as_float(r.w));
                         acc[4 * u + 0] += f.x; acc[4 * u + 1] += f.y; acc[4 * u + 2] += f.z; acc[4 * u + 3] += f.w;
                     }
                 }
@@ -640,7 +642,7 @@ __global__ void __launch_bounds__(256) arrow_fused_small_kernel(FusedArgs a) {
             const double* npi = a.np + int64_t(t & 1) * G * k;
             for (int c = threadIdx.x; c < T * V; c += blockDim.x) {
                 double acc = 0.0;
-                for (int64_t b = 0; b < G; ++b) acc += npi[b * k + c];
+                for (int64_t b = 0; b < G; ++b) acc += __ldcg(npi + b * k + c);
                 scl_s[c] = acc > 0.0 ? float(1.0 / sqrt(acc)) : 1.0f;
             }
             __syncthreads();
@@ -656,7 +658,7 @@ __global__ void __launch_bounds__(256) arrow_fused_small_kernel(FusedArgs a) {
         for (int v = 0; v < V; ++v) scl[v] = scl_s[col0 + v];
         TX* dst = static_cast<TX*>(a.Y);
         for (int64_t v = gteam; v < a.n; v += nteams) {
-            uint4 o = ld_x(cur + int64_t(__ldg(a.perm0 + v)) * k + col0);
+            uint4 o = ld_x_cg(cur + int64_t(__ldg(a.perm0 + v)) * k + col0);
             if (RESCALE) {
                 float f[V];
                 P::to_float(o, f);

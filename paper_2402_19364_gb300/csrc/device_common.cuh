@@ -82,6 +82,20 @@ __device__ __forceinline__ uint4 ld_x(const void* p) {
                  : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
     return r;
 }
+// The same 16 bytes through L2 only (ld.global.cg): for data that other CTAs of the same
+// launch write (the one-launch path's ping-pong buffers and partial sums), which the
+// read-only path (.nc) or L1 could serve stale.
+__device__ __forceinline__ uint4 ld_x_cg(const void* p) {
+    uint4 r;
+    asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+template <bool COHERENT>
+__device__ __forceinline__ uint4 ld_row(const void* p) {
+    if constexpr (COHERENT) return ld_x_cg(p);
+    else return ld_x(p);
+}
+
 // Output rows are written once per iteration and read by the next one, far beyond L2: by
 // default a plain store; ARROW_Y_STORE_CS selects the streaming (evict-first) form.
 #ifndef ARROW_Y_STORE_CS
@@ -171,7 +185,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 #endif
 // R entries j, j + S, ..., j + (R-1) S of a split-row segment (columns and values from
 // global memory), their gathers issued together, accumulated in that order.
-template <int R, typename TX, typename TV, int S>
+template <int R, typename TX, typename TV, int S, bool COHERENT = false>
 __device__ __forceinline__ void segment_tail(const int32_t* __restrict__ col, const TV* __restrict__ val,
                                              const TX* __restrict__ X, int64_t ldx, int j, float* acc) {
     using P = Pack<TX>;
@@ -184,7 +198,7 @@ __device__ __forceinline__ void segment_tail(const int32_t* __restrict__ col, co
 #pragma unroll
     for (int u = 0; u < R; ++u) w[u] = val_to_float(ld_stream_val<TV>(val + j + u * S));
 #pragma unroll
-    for (int u = 0; u < R; ++u) x[u] = ld_x(X + int64_t(c[u]) * ldx);
+    for (int u = 0; u < R; ++u) x[u] = ld_row<COHERENT>(X + int64_t(c[u]) * ldx);
 #pragma unroll
     for (int u = 0; u < R; ++u) {
         float f[V];
@@ -194,7 +208,7 @@ __device__ __forceinline__ void segment_tail(const int32_t* __restrict__ col, co
     }
 }
 
-template <typename TX, typename TV, int T, int U = 8>
+template <typename TX, typename TV, int T, int U = 8, bool COHERENT = false>
 __device__ __forceinline__ void segment_partial(const int32_t* __restrict__ col, const TV* __restrict__ val,
                                                       const TX* __restrict__ X, int64_t ldx, int s, int e, int lane,
                                                       float* acc) {
@@ -215,7 +229,7 @@ __device__ __forceinline__ void segment_partial(const int32_t* __restrict__ col,
 #pragma unroll
         for (int u = 0; u < U; ++u) w[u] = val_to_float(ld_stream_val<TV>(val + j + u * TPW));
 #pragma unroll
-        for (int u = 0; u < U; ++u) x[u] = ld_x(X + int64_t(c[u]) * ldx);
+        for (int u = 0; u < U; ++u) x[u] = ld_row<COHERENT>(X + int64_t(c[u]) * ldx);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             float f[V];
@@ -228,31 +242,31 @@ __device__ __forceinline__ void segment_partial(const int32_t* __restrict__ col,
     // the team's last 0..U-1 entries j, j + TPW, ...: one round of exactly that many gathers
     // (one at a time, each would wait a full latency); same order of accumulation
     switch (j < e ? (e - j + TPW - 1) / TPW : 0) {
-        case 7: segment_tail<7, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
-        case 6: segment_tail<6, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
-        case 5: segment_tail<5, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
-        case 4: segment_tail<4, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
-        case 3: segment_tail<3, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
-        case 2: segment_tail<2, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
-        case 1: segment_tail<1, TX, TV, TPW>(col, val, X, ldx, j, acc); break;
+        case 7: segment_tail<7, TX, TV, TPW, COHERENT>(col, val, X, ldx, j, acc); break;
+        case 6: segment_tail<6, TX, TV, TPW, COHERENT>(col, val, X, ldx, j, acc); break;
+        case 5: segment_tail<5, TX, TV, TPW, COHERENT>(col, val, X, ldx, j, acc); break;
+        case 4: segment_tail<4, TX, TV, TPW, COHERENT>(col, val, X, ldx, j, acc); break;
+        case 3: segment_tail<3, TX, TV, TPW, COHERENT>(col, val, X, ldx, j, acc); break;
+        case 2: segment_tail<2, TX, TV, TPW, COHERENT>(col, val, X, ldx, j, acc); break;
+        case 1: segment_tail<1, TX, TV, TPW, COHERENT>(col, val, X, ldx, j, acc); break;
         default: break;
     }
 #else
-    for (; j < e; j += TPW) segment_tail<1, TX, TV, TPW>(col, val, X, ldx, j, acc);
+    for (; j < e; j += TPW) segment_tail<1, TX, TV, TPW, COHERENT>(col, val, X, ldx, j, acc);
 #endif
 }
 
 // One gather round of a row staged in shared memory: the R entries base..base+R-1 (column
 // and value from shared memory), their 16-byte X gathers issued together, then accumulated
 // into acc in entry order.
-template <int R, typename TX, typename TV>
+template <int R, typename TX, typename TV, bool COHERENT = false>
 __device__ __forceinline__ void gather_round(const int32_t* scol, const TV* sval, int base, const TX* X, int64_t ldx,
                                              float* acc) {
     using P = Pack<TX>;
     constexpr int V = P::V;
     uint4 x[R];
 #pragma unroll
-    for (int u = 0; u < R; ++u) x[u] = ld_x(X + int64_t(scol[base + u]) * ldx);
+    for (int u = 0; u < R; ++u) x[u] = ld_row<COHERENT>(X + int64_t(scol[base + u]) * ldx);
 #pragma unroll
     for (int u = 0; u < R; ++u) {
         const float w = val_to_float(sval[base + u]);
@@ -291,19 +305,19 @@ __device__ __forceinline__ void gather_round_upto(const int32_t* scol, const TV*
 // still issue their instructions (a 9-entry row spent 16 slots); the exact round costs a
 // divergent branch when the teams of a warp have different remainders, which is cheap when a
 // warp holds few teams (wide rows) and costly when it holds many (see gather_row_pred).
-template <typename TX, typename TV>
+template <typename TX, typename TV, bool COHERENT = false>
 __device__ __forceinline__ void gather_row(const int32_t* scol, const TV* sval, int s, int e, const TX* X, int64_t ldx,
                                            float* acc) {
     int base = s;
-    for (; base + 8 <= e; base += 8) gather_round<8>(scol, sval, base, X, ldx, acc);
+    for (; base + 8 <= e; base += 8) gather_round<8, TX, TV, COHERENT>(scol, sval, base, X, ldx, acc);
     switch (e - base) {
-        case 7: gather_round<7>(scol, sval, base, X, ldx, acc); break;
-        case 6: gather_round<6>(scol, sval, base, X, ldx, acc); break;
-        case 5: gather_round<5>(scol, sval, base, X, ldx, acc); break;
-        case 4: gather_round<4>(scol, sval, base, X, ldx, acc); break;
-        case 3: gather_round<3>(scol, sval, base, X, ldx, acc); break;
-        case 2: gather_round<2>(scol, sval, base, X, ldx, acc); break;
-        case 1: gather_round<1>(scol, sval, base, X, ldx, acc); break;
+        case 7: gather_round<7, TX, TV, COHERENT>(scol, sval, base, X, ldx, acc); break;
+        case 6: gather_round<6, TX, TV, COHERENT>(scol, sval, base, X, ldx, acc); break;
+        case 5: gather_round<5, TX, TV, COHERENT>(scol, sval, base, X, ldx, acc); break;
+        case 4: gather_round<4, TX, TV, COHERENT>(scol, sval, base, X, ldx, acc); break;
+        case 3: gather_round<3, TX, TV, COHERENT>(scol, sval, base, X, ldx, acc); break;
+        case 2: gather_round<2, TX, TV, COHERENT>(scol, sval, base, X, ldx, acc); break;
+        case 1: gather_round<1, TX, TV, COHERENT>(scol, sval, base, X, ldx, acc); break;
         default: break;
     }
 }
