@@ -62,7 +62,7 @@ def parse():
                    help="skip timing the decomposition with its steps on the GPU")
     p.add_argument("--no-sub", action="store_true", help="default workload only: skip the other configurations' records")
     p.add_argument("--sub", default="grid2d,rmat,batch,serve,predicates", help="which other configurations to attach")
-    p.add_argument("--tuning", default="", help="tile_rows,tile_nnz,ctas_per_sm,carveout[,fold_permute_in]: fixed tuning "
+    p.add_argument("--tuning", default="", help="tile_rows,tile_nnz,ctas_per_sm,carveout[,fold_permute_in[,fused_small]]: fixed tuning "
                    "instead of autotuning (keeps a profiler's launch list short)")
     return p.parse_args()
 
@@ -72,8 +72,8 @@ def fixed_tuning(a):
     if not a.tuning:
         return None
     t = tuple(int(v) for v in a.tuning.split(","))
-    if len(t) not in (4, 5):
-        raise SystemExit("--tuning wants tile_rows,tile_nnz,ctas_per_sm,carveout[,fold_permute_in]")
+    if len(t) not in (4, 5, 6):
+        raise SystemExit("--tuning wants tile_rows,tile_nnz,ctas_per_sm,carveout[,fold_permute_in[,fused_small]]")
     return t
 
 
