@@ -961,10 +961,12 @@ static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags,
     p.x_bytes = align256(size_t(h->n) * size_t(k) * sx);
     p.part_bytes = align256(std::max<size_t>(1, h->seg_begin.size()) * size_t(p.kc) * 4);
     // the one-launch path: asked for by the tuning, for one-chunk k and small problems (where
-    // kernel start-up dominates), one CTA per 4 rows per team, at most one per SM (all resident)
+    // kernel start-up dominates), one row per team and phase where the SMs allow (each row is a
+    // chain of dependent loads, so rows per team add latency), at most one CTA per SM (all
+    // resident)
     p.fused_grid = 0;
     if (h->tune.fused_small && p.chunks == 1 && fused_eligible(h, k, x_dtype)) {
-        const int64_t per_cta = int64_t(256 / p.T) * 4;
+        const int64_t per_cta = int64_t(256 / p.T);
         p.fused_grid = int(std::max<int64_t>(1, std::min<int64_t>((h->n + per_cta - 1) / per_cta, sm)));
     }
     const size_t np_slots = std::max<size_t>(size_t(p.rows_grid + p.comb_grid), size_t(2 * p.fused_grid));
