@@ -59,7 +59,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 // kernels
 // ------------------------------------------------------------------------------------
 // dynamic shared memory: pipeline state, kStages tile buffers and, with the rescale, the
-// per-team FP64 column sums of squares (256 / T teams x kc = T V columns: 256 V doubles)
+// per-warp FP64 column sums of squares (8 warps x kc columns)
 static inline int rows_smem_bytes(const TileLayout& L, int norm_doubles) { return 128 + kStages * L.buf + 8 * norm_doubles; }
 
 struct RowArgs {
@@ -108,6 +108,25 @@ __device__ __forceinline__ void apply_sigma(float* acc, int sigma, int lane) {
     }
 }
 
+// A warp's FP32 squares (V columns per lane, teams of T lanes) added to the warp's FP64
+// column sums slot: converted to FP64, summed over the warp's teams by a fixed xor butterfly,
+// and added by the first team, which owns these columns of the slot.  Resets sq.  Called
+// by all 32 lanes of the warp together.
+template <int T, int V>
+__device__ __forceinline__ void flush_squares(float* sq, double* slot, int lane) {
+    double d[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) { d[v] = double(sq[v]); sq[v] = 0.f; }
+#pragma unroll
+    for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < V; ++v) d[v] += __shfl_xor_sync(0xffffffffu, d[v], off);
+    if (lane < T) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) slot[v] += d[v];
+    }
+}
+
 // Thread 0: stage tile t (row pointers, columns, values) into buf with three bulk copies.
 template <typename TV>
 __device__ __forceinline__ void issue_tile(const RowArgs& a, int t, unsigned char* buf, uint64_t* bar) {
@@ -133,7 +152,7 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
     extern __shared__ __align__(128) unsigned char smem[];
     PipeSmem* ps = reinterpret_cast<PipeSmem*>(smem);
     unsigned char* bufs = smem + 128;
-    double* wsum = reinterpret_cast<double*>(smem + 128 + kStages * a.buf_bytes);   // [TEAMS][kc]
+    double* wsum = reinterpret_cast<double*>(smem + 128 + kStages * a.buf_bytes);   // [NW warps][kc]
     const int lane = threadIdx.x & 31;
     const int tl = threadIdx.x & (T - 1);
     const int team = threadIdx.x / T;
@@ -152,7 +171,7 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
         fence_mbar_init();
     }
     if (RESCALE)
-        for (int c = threadIdx.x; c < TEAMS * a.kc; c += blockDim.x) wsum[c] = 0.0;
+        for (int c = threadIdx.x; c < NW * a.kc; c += blockDim.x) wsum[c] = 0.0;
     __syncthreads();
     if (threadIdx.x == 0)
         for (int b = 0; b < kStages; ++b)
@@ -208,10 +227,9 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
             }
         }
         if (RESCALE && (i & 7) == 7) {
-            // every 8 tiles each lane adds its FP32 squares to its team's FP64 column sums
-            // (the lane owns these columns of the slot: no other thread touches them)
-#pragma unroll
-            for (int v = 0; v < V; ++v) { wsum[team * a.kc + col0 + v] += double(sq[v]); sq[v] = 0.f; }
+            // every 8 tiles the lanes' FP32 squares go into the warp's FP64 column sums: a fixed
+            // xor butterfly over the warp's teams, then the first team adds (it owns the slot)
+            flush_squares<T, V>(sq, wsum + (threadIdx.x >> 5) * a.kc + col0, lane);
         }
         __syncwarp();
         if (lane == 0)
@@ -223,19 +241,17 @@ __global__ void __launch_bounds__(256, RESCALE ? ARROW_ROWS_MIN_BLOCKS_RESCALE :
                 }
             });
     }
-    if (RESCALE)
-#pragma unroll
-        for (int v = 0; v < V; ++v) wsum[team * a.kc + col0 + v] += double(sq[v]);
+    if (RESCALE) flush_squares<T, V>(sq, wsum + (threadIdx.x >> 5) * a.kc + col0, lane);
     __syncthreads();
     if (ps->failed) {
         if (threadIdx.x == 0) drain_pipeline(ps);
         return;
     }
     if (RESCALE) {
-        // block's FP64 column sums: teams in fixed order
+        // block's FP64 column sums: warps in fixed order
         for (int c = threadIdx.x; c < a.kc; c += blockDim.x) {
             double acc = 0.0;
-            for (int t2 = 0; t2 < TEAMS; ++t2) acc += wsum[t2 * a.kc + c];
+            for (int w = 0; w < NW; ++w) acc += wsum[w * a.kc + c];
             a.norm_partials[int64_t(blockIdx.x) * a.ldx + a.koff + c] = acc;
         }
     }
@@ -999,7 +1015,7 @@ static void launch_step(const arrow_handle_s* h, const Plan& p, const TX* cur, T
         const TileLayout L = tile_layout(h->tune.tile_rows, h->tune.tile_nnz);
         RowArgs ra{d.rowptr, col, d.val, d.tile_row, d.tile_ent, n_tiles, cur, nxt, k, koff, p.kc, scale_in, np,
                    d.status, L.rp, L.col, L.buf, sigma};
-        const int smem = rows_smem_bytes(L, np ? (256 / T) * p.kc : 0);
+        const int smem = rows_smem_bytes(L, np ? 8 * p.kc : 0);
         cudaEvent_t e0 = pf.begin();
         if (np) {
             set_smem_attrs(reinterpret_cast<const void*>(arrow_rows_kernel<TX, TV, T, true>), h->tune.carveout);
@@ -1533,7 +1549,8 @@ int arrow_autotune(arrow_handle h, const void* X, void* Y, int64_t k, int32_t it
         for (int ctas = 2; ctas <= ARROW_ROWS_MIN_BLOCKS && rc == ARROW_OK; ++ctas) {
             if ((flags & ARROW_RESCALE) && ctas > ARROW_ROWS_MIN_BLOCKS_RESCALE) break;
             const TileLayout L = tile_layout(sh[0], sh[1]);
-            const int per = rows_smem_bytes(L, (flags & ARROW_RESCALE) ? 256 * int(16 / dtype_size(x_dtype)) : 0) + 1024;
+            const int64_t kcw = std::min<int64_t>(k, 32 * int64_t(16 / dtype_size(x_dtype)));
+            const int per = rows_smem_bytes(L, (flags & ARROW_RESCALE) ? 8 * int(kcw) : 0) + 1024;
             if (ctas * per > 227 * 1024) break;
             const int pct = std::min(100, (ctas * per * 100 + 228 * 1024 - 1) / (228 * 1024) + 5);
             arrow_tuning cand{sh[0], sh[1], ctas, pct, h->tune.fold_permute_in, 0};
