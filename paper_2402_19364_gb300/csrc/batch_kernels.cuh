@@ -65,6 +65,13 @@ inline int batch_smem_bytes(const TileLayout& L) { return 128 + kStages * L.buf;
 #ifndef ARROW_BATCH_MIN_BLOCKS
 #define ARROW_BATCH_MIN_BLOCKS 4
 #endif
+// 1: a team sums two rows at a time (gather_row_pair_pred: 4 slots each per round of 8, which
+// needs 80 registers, i.e. 3 CTAs/SM); 0: one row at a time.  256 random-geometric matrices:
+// 48.5 k matrix-iterations/s with pairs at 3 CTAs/SM, 47.6 k one row at a time at 4 (within run
+// to run spread), 35.1 k with pairs squeezed into 64 registers (spills).
+#ifndef ARROW_BATCH_PAIRS
+#define ARROW_BATCH_PAIRS 0
+#endif
 constexpr int kBatchMinBlocks = ARROW_BATCH_MIN_BLOCKS;
 
 template <typename TX, typename TV>
@@ -123,6 +130,20 @@ __global__ void __launch_bounds__(256, kBatchMinBlocks) arrow_batch_rows_kernel(
         const int32_t* scol = reinterpret_cast<const int32_t*>(buf + a.rp_bytes) + (e0 & 3);
         const TV* sval = reinterpret_cast<const TV*>(buf + a.rp_bytes + a.col_bytes) + (e0 & (VE - 1));
         const int nrows = r1 - r0;
+#if ARROW_BATCH_PAIRS
+        // two rows per team at a time (gather_row_pair_pred)
+        for (int j = team; j < nrows; j += 2 * teams) {
+            const int j2 = j + teams;
+            const int s = srp[j] - e0, e = srp[j + 1] - e0;
+            const int s2 = j2 < nrows ? srp[j2] - e0 : 0, e2 = j2 < nrows ? srp[j2 + 1] - e0 : 0;
+            float acc[V], acc2[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) { acc[v] = 0.f; acc2[v] = 0.f; }
+            gather_row_pair_pred<TX, TV>(scol, sval, s, e, s2, e2, X, ldx, acc, acc2);
+            *reinterpret_cast<uint4*>(Y + int64_t(r0 + j) * ldx) = P::from_float(acc);
+            if (j2 < nrows) *reinterpret_cast<uint4*>(Y + int64_t(r0 + j2) * ldx) = P::from_float(acc2);
+        }
+#else
         for (int j = team; j < nrows; j += teams) {
             const int s = srp[j] - e0, e = srp[j + 1] - e0;
             float acc[V];
@@ -131,6 +152,7 @@ __global__ void __launch_bounds__(256, kBatchMinBlocks) arrow_batch_rows_kernel(
             gather_row_pred<TX, TV>(scol, sval, s, e, X, ldx, acc);
             *reinterpret_cast<uint4*>(Y + int64_t(r0 + j) * ldx) = P::from_float(acc);
         }
+#endif
         __syncwarp();
         if (lane == 0)
             release_buffer(ps, b, NW, [&](int bb) {

@@ -330,6 +330,46 @@ __device__ __forceinline__ void gather_row_pred(const int32_t* scol, const TV* s
     for (int base = s; base < e; base += 8) gather_round_upto<8>(scol, sval, base, e - base, X, ldx, acc);
 }
 
+// Two rows of a staged tile summed together: rounds of 8 gathers, the first 4 slots for row A
+// and the last 4 for row B (slots past a row's end predicated off), each row accumulated in its
+// own entry order.  A 9-entry row alone takes 2 rounds of 8 slots; two of them together take 3.
+template <typename TX, typename TV>
+__device__ __forceinline__ void gather_row_pair_pred(const int32_t* scol, const TV* sval, int sa, int ea, int sb,
+                                                     int eb, const TX* X, int64_t ldx, float* acca, float* accb) {
+    using P = Pack<TX>;
+    constexpr int V = P::V;
+    for (int a = sa, b = sb; a < ea || b < eb; a += 4, b += 4) {
+        const int ca = ea - a, cb = eb - b;
+        uint4 xa[4], xb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (u < ca) xa[u] = ld_x(X + int64_t(scol[a + u]) * ldx);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (u < cb) xb[u] = ld_x(X + int64_t(scol[b + u]) * ldx);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (u < ca) {
+                const float w = val_to_float(sval[a + u]);
+                float f[V];
+                P::to_float(xa[u], f);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acca[v] = fmaf(w, f[v], acca[v]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (u < cb) {
+                const float w = val_to_float(sval[b + u]);
+                float f[V];
+                P::to_float(xb[u], f);
+#pragma unroll
+                for (int v = 0; v < V; ++v) accb[v] = fmaf(w, f[v], accb[v]);
+            }
+        }
+    }
+}
+
 // Tile pipeline state at the start of dynamic shared memory (128 bytes): one "full"
 // mbarrier per staging buffer (completed by the buffer's bulk copies), the number of warps
 // done with the buffer's current use, the buffer's issued uses, and a small header.

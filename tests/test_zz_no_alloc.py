@@ -1,13 +1,14 @@
 """GPU test of arrow_spmm_static, the entry point for callers that cannot allocate.
 
-Some callers cannot call cudaMalloc: code recorded during CUDA graph capture, plugins
-inside a framework that owns all device memory, and serving loops that forbid allocation
-after start-up.  arrow_spmm_static keeps its scratch in a fixed 64 MiB device array of the
-library instead.  This file is collected last so that, should it fail, a run stopping at
+Some callers cannot call cudaMalloc: plugins inside a framework that owns all device memory
+through its own allocator, and serving loops that forbid allocation after start-up (cudaMalloc
+and cudaFree synchronise the device).  arrow_spmm_static keeps its scratch in a fixed 64 MiB
+device array of the library instead.  This file is collected last so that, should it fail, a run stopping at
 the first failure has already run every other test.  It checks, through the C-ABI, that two
 calls in a row give the result of arrow_spmm within the FP32 tolerance of the parity tests
 (max over columns of ||y - y_ref||_inf / ||y_ref||_inf <= 1e-5 * iters), and that a
-problem too large for the array is refused.
+problem too large for the array is refused, and that calls after the first leave the device's
+free memory unchanged.
 """
 import ctypes
 
