@@ -99,3 +99,26 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_subrecords_collect_child_lines_and_errors(monkeypatch):
+    # the default run attaches the other configurations by running bench.py as child processes;
+    # here the children are the CPU-only reference arm (a line comes back) and an unknown option
+    # (the error is recorded, not raised)
+    monkeypatch.setattr(bench, "SUBRECORDS", [
+        ("ok", ["--impl", "reference", "--workload", "grid2d", "--steps", "1", "--warmup", "0"]),
+        ("bad", ["--no-such-option"]),
+        ("skipped", ["--impl", "reference"]),
+    ])
+    recs = bench.run_subrecords(["ok", "bad"], timeout_s=600)
+    assert set(recs) == {"ok", "bad"}
+    assert recs["ok"]["impl"] == "reference" and recs["ok"]["value"] > 0 and recs["ok"]["wall_s"] > 0
+    assert "error" in recs["bad"] and recs["bad"]["error"].startswith("rc=")
+
+
+def test_every_default_subrecord_is_a_known_workload():
+    # the children's arguments parse: each names a workload bench.py knows
+    for key, args in bench.SUBRECORDS:
+        wl = args[args.index("--workload") + 1]
+        assert wl in ("grid2d", "rmat", "batch", "serve", "predicates"), (key, wl)
+    assert [k for k, _ in bench.SUBRECORDS] == ["grid2d", "rmat", "batch", "serve", "predicates"]
