@@ -570,14 +570,15 @@ def run_serve(a):
     print(json.dumps(out), flush=True)
 
 
-def time_calls(arrow, M, Xd, Yd, iters, rescale, steps, warmup, pg, stream, flush=None):
+def time_calls(arrow, M, Xd, Yd, iters, rescale, steps, warmup, pg, stream, flush=None, sigma=None):
     """Warm-up calls, then `steps` timed arrow_spmm calls with CUDA events on the launching
     stream (barrier + synchronize on both sides, max over ranks).  With `flush` (a buffer
     larger than L2) the buffer is written between calls and each call is timed on its own.
     Per-kernel device times come from the library's own events (ARROW_PROFILE)."""
     import torch
+    sigma = sigma or {}
     for _ in range(warmup):
-        M.spmm(Xd, iters, rescale=rescale, out=Yd)
+        M.spmm(Xd, iters, rescale=rescale, out=Yd, **sigma)
     torch.cuda.synchronize()
     for kind in (arrow.ARROW_K_ROWS, arrow.ARROW_K_SEGMENTS, arrow.ARROW_K_NORM, arrow.ARROW_K_PERMUTE,
                  arrow.ARROW_K_FUSED):
@@ -592,7 +593,7 @@ def time_calls(arrow, M, Xd, Yd, iters, rescale, steps, warmup, pg, stream, flus
         if flush is not None:
             flush.fill_(i & 0xff)
         starts[i].record(stream)
-        M.spmm(Xd, iters, rescale=rescale, out=Yd, profile=True)
+        M.spmm(Xd, iters, rescale=rescale, out=Yd, profile=True, **sigma)
         marks[i].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -774,7 +775,8 @@ def run_predicates(a):
     """The two arrow shapes on the GPU (Section 1's band |p - q| <= b against the block-diagonal
     tiles of Section 3.1): levels, non-zero b x b tiles, algorithmic bytes per iteration and the
     measured time of the same product on a 3D 200^3 grid (k = 16 FP32, 20 iterations with the
-    rescale) and an R-MAT scale 21 graph (k = 128 BF16, 8 iterations)."""
+    rescale) and an R-MAT scale 21 graph (k = 128 BF16, 8 iterations); plus the block form's time
+    with the fused sigma epilogues (ReLU and row normalisation) on."""
     import torch
     import workloads as w
     from paper_2402_19364_gb300 import build as _build
@@ -804,6 +806,11 @@ def run_predicates(a):
                          "ms_per_iter": tm["ms_total"] / max(3, a.steps) / iters,
                          "rows_segments_ms_per_iter": (tm["kernel_ms"]["rows"] + tm["kernel_ms"]["segments"])
                          / max(1, tm["rows_launches"])}
+            if pred == "block":
+                # the same product with sigma = rownorm(relu(.)) fused into the row stores
+                ts = time_calls(arrow, M, X, torch.empty_like(X), iters, rs, max(3, a.steps), 3, None, stream,
+                                sigma={"relu": True, "rownorm": True})
+                rec["block_relu_rownorm_ms_per_iter"] = ts["ms_total"] / max(3, a.steps) / iters
             Yf = Y.float()
             if ref is None:
                 ref = Yf

@@ -85,6 +85,27 @@ def test_static_scratch_allocates_nothing(arrow):
     assert free1 == free0
 
 
+def test_static_scratch_one_launch_path(arrow):
+    """The one-launch path (tuning fused_small) through the static scratch: the same bits as
+    arrow_spmm on that path, two calls in a row."""
+    from paper_2402_19364_gb300 import _native
+    L = _native.lib()
+    A = w.grid2d_64(seed=1)
+    M = arrow.ArrowMatrix(A, 64)
+    t = M.tuning
+    M.set_tuning(t["tile_rows"], t["tile_nnz"], t["ctas_per_sm"], t["carveout"], 0, 1)
+    X = torch.from_numpy(w.features(A.n, 16, seed=2)).cuda()
+    ref = M.spmm(X, 10, rescale=True)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        Y = torch.full_like(X, float("nan"))
+        _native.check(L.arrow_spmm_static(M._h, ctypes.c_void_p(X.data_ptr()), 16, 10, ctypes.c_void_p(Y.data_ptr()),
+                                          _native.ARROW_F32, _native.ARROW_RESCALE,
+                                          ctypes.c_void_p(stream.cuda_stream)))
+        torch.cuda.synchronize()
+        assert torch.equal(Y, ref)
+
+
 def test_static_scratch_refuses_large_problems(arrow):
     from paper_2402_19364_gb300 import _native
     L = _native.lib()
