@@ -425,6 +425,13 @@ int arrow_status(arrow_handle h, int32_t* status);
  * Touches no handle; the context stays usable.  Errors: ARROW_EINVAL, ARROW_ECUDA. */
 int arrow_selftest_timeout(int64_t limit_ns, int32_t* status);
 
+/* arrow_selftest_grid_timeout -- runs the one-launch path's grid-barrier timeout on purpose: a
+ * cooperative launch of `blocks` blocks (2 <= blocks <= SMs) in which block 0 never arrives, so
+ * every other block's barrier wait gives up after limit_ns (0 < limit <= 10 s) and returns;
+ * *gave_up receives how many blocks gave up (blocks - 1 expected).  Touches no handle; the
+ * context stays usable.  Errors: ARROW_EINVAL, ARROW_ECUDA. */
+int arrow_selftest_grid_timeout(int64_t limit_ns, int32_t blocks, int32_t* gave_up);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* arrow_last_error(void);
 

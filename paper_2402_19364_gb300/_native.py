@@ -122,6 +122,7 @@ SIGNATURES = {
     "arrow_profile_get": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "arrow_status": (_I32, [_P, ctypes.POINTER(_I32)]),
     "arrow_selftest_timeout": (_I32, [_I64, ctypes.POINTER(_I32)]),
+    "arrow_selftest_grid_timeout": (_I32, [_I64, _I32, ctypes.POINTER(_I32)]),
     "arrow_get_tuning": (_I32, [_P, ctypes.POINTER(ArrowTuning)]),
     "arrow_set_tuning": (_I32, [_P, ctypes.POINTER(ArrowTuning)]),
     "arrow_autotune": (_I32, [_P, _P, _P, _I64, _I32, _I32, _I32, _P, ctypes.POINTER(ArrowTuning),

@@ -687,6 +687,13 @@ __global__ void __launch_bounds__(256) arrow_fused_small_kernel(FusedArgs a) {
     }
 }
 
+// Self-test of the grid barrier's bounded wait: block 0 never arrives, so every other block's
+// wait must give up after limit_ns; each block that gave up adds 1 to status[0].
+__global__ void arrow_selftest_grid_kernel(unsigned* bar, int32_t* status, uint64_t limit_ns) {
+    if (blockIdx.x == 0) return;
+    if (!grid_barrier(bar, bar + 1, gridDim.x, limit_ns) && threadIdx.x == 0) atomicAdd(status, 1);
+}
+
 template <typename TV>
 __global__ void arrow_convert_values_kernel(const double* __restrict__ src, TV* __restrict__ dst, int64_t n);
 template <>
@@ -1710,6 +1717,37 @@ int arrow_selftest_timeout(int64_t limit_ns, int32_t* status) {
     if (e == cudaSuccess) e = cudaMemcpy(status, d, sizeof(int32_t), cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(e, "arrow_selftest_timeout");
+    return ARROW_OK;
+}
+
+int arrow_selftest_grid_timeout(int64_t limit_ns, int32_t blocks, int32_t* gave_up) {
+    if (!gave_up || limit_ns <= 0 || limit_ns > 10000000000ll || blocks < 2) {
+        set_error("arrow_selftest_grid_timeout: gave_up NULL, blocks < 2 or limit outside (0, 10 s]");
+        return ARROW_EINVAL;
+    }
+    int dev = 0, sms = 0, coop = 0;
+    ACK(cudaGetDevice(&dev));
+    ACK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ACK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop || blocks > sms) {
+        set_error("arrow_selftest_grid_timeout: needs cooperative launch and at most one block per SM");
+        return ARROW_EINVAL;
+    }
+    int32_t* d = nullptr;
+    ACK(cudaMalloc(&d, 4 * sizeof(int32_t)));
+    cudaError_t e = cudaMemset(d, 0, 4 * sizeof(int32_t));
+    if (e == cudaSuccess) {
+        unsigned* bar = reinterpret_cast<unsigned*>(d + 2);
+        int32_t* st = d;
+        uint64_t lim = uint64_t(limit_ns);
+        void* args[] = {&bar, &st, &lim};
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(arrow_selftest_grid_kernel), dim3(blocks),
+                                        dim3(64), args, 0, nullptr);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(gave_up, d, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "arrow_selftest_grid_timeout");
     return ARROW_OK;
 }
 

@@ -332,6 +332,11 @@ def test_status_word_and_bounded_wait_selftest(arrow):
     t0 = time.time()
     _native.check(_native.lib().arrow_selftest_timeout(50_000_000, ctypes.byref(st)))
     assert st.value == 1 and time.time() - t0 < 5.0            # gave up after ~50 ms, reported it
+    # the one-launch path's grid barrier: one block never arrives, the other 15 give up
+    gave = ctypes.c_int32(-1)
+    t0 = time.time()
+    _native.check(_native.lib().arrow_selftest_grid_timeout(50_000_000, 16, ctypes.byref(gave)))
+    assert gave.value == 15 and time.time() - t0 < 5.0
     Y = M.spmm(torch.ones(A.n, 16, device="cuda"), 2)          # context still usable
     assert torch.allclose(Y, torch.ones_like(Y), atol=1e-5)
 
