@@ -54,6 +54,14 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 #ifndef ARROW_ROWS_EXACT
 #define ARROW_ROWS_EXACT 1
 #endif
+// CTAs per SM of the split-row combine kernel's grid (and its launch bound), without and with
+// the FP64 rescale (whose per-lane FP64 sums need more registers).
+#ifndef ARROW_COMB_CTAS_PER_SM
+#define ARROW_COMB_CTAS_PER_SM 6
+#endif
+#ifndef ARROW_COMB_CTAS_PER_SM_RESCALE
+#define ARROW_COMB_CTAS_PER_SM_RESCALE 4
+#endif
 
 // ------------------------------------------------------------------------------------
 // kernels
@@ -328,7 +336,8 @@ struct CombArgs {
 // Second stage of the head-row reduction: a team per split row adds its segment partials
 // in segment order, scales and stores the row (overwriting the zero the rows kernel wrote).
 template <typename TX, int T, bool RESCALE>
-__global__ void __launch_bounds__(256) arrow_combine_kernel(CombArgs a) {
+__global__ void __launch_bounds__(256, RESCALE ? ARROW_COMB_CTAS_PER_SM_RESCALE : ARROW_COMB_CTAS_PER_SM)
+    arrow_combine_kernel(CombArgs a) {
     using P = Pack<TX>;
     constexpr int V = P::V;
     const int lane = threadIdx.x & 31;
@@ -348,7 +357,24 @@ __global__ void __launch_bounds__(256) arrow_combine_kernel(CombArgs a) {
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = 0.f;
         const int g0 = __ldg(a.long_segptr + li), g1 = __ldg(a.long_segptr + li + 1);
-        for (int g = g0; g < g1; ++g) {
+        int g = g0;
+        for (; g + 1 < g1; g += 2) {
+            // two segments' partials loaded together, added in segment order
+            const float4* p = reinterpret_cast<const float4*>(a.partials + int64_t(g) * a.kc + col0);
+            const float4* p2 = reinterpret_cast<const float4*>(a.partials + int64_t(g + 1) * a.kc + col0);
+            float4 f[V / 4], f2[V / 4];
+#pragma unroll
+            for (int q = 0; q < V / 4; ++q) { f[q] = p[q]; f2[q] = p2[q]; }
+#pragma unroll
+            for (int q = 0; q < V / 4; ++q) {
+                acc[4 * q + 0] += f[q].x; acc[4 * q + 1] += f[q].y; acc[4 * q + 2] += f[q].z; acc[4 * q + 3] += f[q].w;
+            }
+#pragma unroll
+            for (int q = 0; q < V / 4; ++q) {
+                acc[4 * q + 0] += f2[q].x; acc[4 * q + 1] += f2[q].y; acc[4 * q + 2] += f2[q].z; acc[4 * q + 3] += f2[q].w;
+            }
+        }
+        if (g < g1) {
             const float4* p = reinterpret_cast<const float4*>(a.partials + int64_t(g) * a.kc + col0);
 #pragma unroll
             for (int q = 0; q < V / 4; ++q) {
@@ -979,7 +1005,11 @@ static int make_plan(const arrow_handle_s* h, int64_t k, int x_dtype, int flags,
     p.rows_grid = int(std::max<int64_t>(1, std::min<int64_t>(n_tiles, int64_t(sm) * std::min(h->tune.ctas_per_sm, cap))));
     const int64_t n_long = int64_t(h->long_rows.size());
     const int64_t teams = 256 / p.T;
-    p.comb_grid = n_long ? int(std::max<int64_t>(1, std::min<int64_t>((n_long + teams - 1) / teams, int64_t(sm) * 2))) : 0;
+    // combine kernel: as many CTAs per SM as its launch bound allows (each team has only a split
+    // row's few partial loads in flight, so occupancy is what hides their latency)
+    const int comb_cap = (flags & ARROW_RESCALE) ? ARROW_COMB_CTAS_PER_SM_RESCALE : ARROW_COMB_CTAS_PER_SM;
+    p.comb_grid =
+        n_long ? int(std::max<int64_t>(1, std::min<int64_t>((n_long + teams - 1) / teams, int64_t(sm) * comb_cap))) : 0;
     const size_t sx = dtype_size(x_dtype);
     p.x_bytes = align256(size_t(h->n) * size_t(k) * sx);
     p.part_bytes = align256(std::max<size_t>(1, h->seg_begin.size()) * size_t(p.kc) * 4);
