@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
 #include <utility>
 #include <vector>
@@ -12,6 +14,25 @@
 namespace arrow {
 
 void set_error(const std::string& msg);
+
+// Allocator whose resize leaves trivially constructible elements uninitialised: large host
+// arrays that are always written in full (in parallel) before they are read, where a
+// value-initialising resize would first be a serial pass over gigabytes.
+template <class T>
+struct DefaultInitAlloc : std::allocator<T> {
+    using value_type = T;
+    DefaultInitAlloc() = default;
+    template <class U>
+    DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
+    template <class U>
+    struct rebind { using other = DefaultInitAlloc<U>; };
+    template <class U>
+    void construct(U* p) noexcept { ::new (static_cast<void*>(p)) U; }
+    template <class U, class... Args>
+    void construct(U* p, Args&&... args) { ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...); }
+};
+template <class T>
+using uvec = std::vector<T, DefaultInitAlloc<T>>;
 
 // ARROW_OK when `device` is the calling thread's current CUDA device; otherwise ARROW_EINVAL
 // (message names `what`) or ARROW_ECUDA.  Every entry point that launches kernels on a
@@ -89,10 +110,10 @@ struct arrow_handle_s {
     int64_t b = 0;
     arrow_opts opts{};
     // copy of the input (values and pattern), kept for the structure export
-    std::vector<int64_t> rowptr;
-    std::vector<int32_t> colidx;
-    std::vector<double> values;
-    std::vector<uint8_t> entry_level;   // level of every entry of A
+    arrow::uvec<int64_t> rowptr;
+    arrow::uvec<int32_t> colidx;
+    arrow::uvec<double> values;
+    arrow::uvec<uint8_t> entry_level;   // level of every entry of A
     std::vector<arrow::Level> levels;
     // fused row program on the host (rows in pi_0 order), uploaded by arrow_upload
     std::vector<int32_t> f_rowptr;      // [n+1] short rows; split rows have no entries here

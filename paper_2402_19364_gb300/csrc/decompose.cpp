@@ -42,24 +42,6 @@ namespace {
 
 int g_threads = 1;
 
-// Allocator whose resize leaves trivially constructible elements uninitialised: the large
-// per-level arrays below are always written in full (in parallel) before they are read, and
-// value-initialising them first would be a serial pass over gigabytes.
-template <class T>
-struct DefaultInitAlloc : std::allocator<T> {
-    using value_type = T;
-    DefaultInitAlloc() = default;
-    template <class U>
-    DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
-    template <class U>
-    struct rebind { using other = DefaultInitAlloc<U>; };
-    template <class U>
-    void construct(U* p) noexcept { ::new (static_cast<void*>(p)) U; }
-    template <class U, class... Args>
-    void construct(U* p, Args&&... args) { ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...); }
-};
-template <class T>
-using uvec = std::vector<T, DefaultInitAlloc<T>>;
 
 // f(begin, end, thread) over [0, n) in g_threads contiguous chunks.
 template <class F>
@@ -641,9 +623,17 @@ int decompose_host(arrow_handle_s* h, const arrow_csr* A, int64_t b, const arrow
     const int64_t n = A->n, nnz = A->nnz;
     const int max_levels = o.max_levels > 0 ? std::min(o.max_levels, 254) : 254;
     h->n = n; h->nnz = nnz; h->b = b; h->opts = o;
-    h->rowptr.assign(A->rowptr, A->rowptr + n + 1);
-    h->colidx.assign(A->colidx, A->colidx + nnz);
-    h->values.assign(A->values, A->values + nnz);
+    // the input copy, in parallel chunks (first touch of gigabytes of new pages)
+    h->rowptr.resize(n + 1);
+    h->colidx.resize(nnz);
+    h->values.resize(nnz);
+    pfor(n + 1, [&](int64_t bb, int64_t e, int) {
+        std::memcpy(h->rowptr.data() + bb, A->rowptr + bb, size_t(e - bb) * sizeof(int64_t));
+    });
+    pfor(nnz, [&](int64_t bb, int64_t e, int) {
+        std::memcpy(h->colidx.data() + bb, A->colidx + bb, size_t(e - bb) * sizeof(int32_t));
+        std::memcpy(h->values.data() + bb, A->values + bb, size_t(e - bb) * sizeof(double));
+    });
 
     SymPattern S;
     build_sym(A, S);
@@ -953,7 +943,7 @@ struct Writer {
         if (n && std::fwrite(p, 1, n, f) != n) ok = false;
     }
     template <class T> void val(const T& v) { raw(&v, sizeof(T)); }
-    template <class T> void vec(const std::vector<T>& v) {
+    template <class T, class Al> void vec(const std::vector<T, Al>& v) {
         val(int64_t(v.size()));
         raw(v.data(), v.size() * sizeof(T));
     }
@@ -969,7 +959,7 @@ struct Reader {
         for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
     }
     template <class T> void val(T& v) { raw(&v, sizeof(T)); }
-    template <class T> void vec(std::vector<T>& v, int64_t max_len) {
+    template <class T, class Al> void vec(std::vector<T, Al>& v, int64_t max_len) {
         int64_t n = -1;
         val(n);
         if (!ok || n < 0 || n > max_len) { ok = false; return; }
